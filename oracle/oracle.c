@@ -1,0 +1,366 @@
+/*
+ * oracle.c -- FP64 reference for E-A-HALS, written from the paper
+ * (Ang & Gillis, arXiv 1805.06604).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by tests/, the smoke check and the
+ * benchmark's CPU-baseline leg.  It shares nothing with the CUDA library.
+ *
+ * Plain loops in double precision; the only freedom taken is the loop
+ * nesting of sums whose order the paper does not fix.  Build with
+ * -ffp-contract=off so that x86-64 and aarch64 give identical bits.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static double *orc_alloc(int64_t count)
+{
+    double *p = (double *)calloc((size_t)(count > 0 ? count : 1), sizeof(double));
+    if (!p) abort();
+    return p;
+}
+
+/* Remark 1: the constant term ||X||_F^2 = <X, X>. */
+double orc_fro2(const orc_matrix *X)
+{
+    double s = 0.0;
+    if (X->is_csr) {
+        int64_t nnz = X->rowptr[X->m];
+        for (int64_t p = 0; p < nnz; ++p) s += X->val[p] * X->val[p];
+    } else {
+        for (int64_t i = 0; i < X->m; ++i)
+            for (int64_t j = 0; j < X->n; ++j) {
+                double v = X->x[i * X->n + j];
+                s += v * v;
+            }
+    }
+    return s;
+}
+
+/* A(k,j) = sum_i W(i,k) X(i,j): the product W^T X of the HALS closed form
+ * (Sec. 1).  Summed over i in increasing order. */
+void orc_wtx(const orc_matrix *X, int r, const double *W, double *A)
+{
+    const int64_t m = X->m, n = X->n;
+    memset(A, 0, sizeof(double) * (size_t)r * (size_t)n);
+    for (int64_t i = 0; i < m; ++i) {
+        if (X->is_csr) {
+            for (int64_t p = X->rowptr[i]; p < X->rowptr[i + 1]; ++p) {
+                int64_t j = X->colidx[p];
+                for (int k = 0; k < r; ++k) A[k * n + j] += W[i * r + k] * X->val[p];
+            }
+        } else {
+            for (int k = 0; k < r; ++k) {
+                double w = W[i * r + k];
+                for (int64_t j = 0; j < n; ++j) A[k * n + j] += w * X->x[i * n + j];
+            }
+        }
+    }
+}
+
+/* C(i,k) = sum_j X(i,j) H(k,j): the product X H^T of Remark 1. */
+void orc_xht(const orc_matrix *X, int r, const double *H, double *C)
+{
+    const int64_t m = X->m, n = X->n;
+    for (int64_t i = 0; i < m; ++i) {
+        for (int k = 0; k < r; ++k) {
+            double s = 0.0;
+            if (X->is_csr) {
+                for (int64_t p = X->rowptr[i]; p < X->rowptr[i + 1]; ++p)
+                    s += X->val[p] * H[k * n + X->colidx[p]];
+            } else {
+                for (int64_t j = 0; j < n; ++j) s += X->x[i * n + j] * H[k * n + j];
+            }
+            C[i * r + k] = s;
+        }
+    }
+}
+
+/* G(k,j) = W(:,k)^T W(:,j). */
+void orc_gram_w(int64_t m, int r, const double *W, double *G)
+{
+    for (int k = 0; k < r; ++k)
+        for (int j = 0; j < r; ++j) {
+            double s = 0.0;
+            for (int64_t i = 0; i < m; ++i) s += W[i * r + k] * W[i * r + j];
+            G[k * r + j] = s;
+        }
+}
+
+/* D(k,j) = H(k,:) H(j,:)^T. */
+void orc_gram_h(int64_t n, int r, const double *H, double *D)
+{
+    for (int k = 0; k < r; ++k)
+        for (int j = 0; j < r; ++j) {
+            double s = 0.0;
+            for (int64_t c = 0; c < n; ++c) s += H[k * n + c] * H[j * n + c];
+            D[k * r + j] = s;
+        }
+}
+
+/* HALS closed form for row k of H (Sec. 1, second line of the display):
+ *   H(k,:) = max(0, (W(:,k)^T X - sum_{j != k} (W(:,k)^T W(:,j)) H(j,:))
+ *                    / ||W(:,k)||^2)
+ * with A = W^T X and G = W^T W, so ||W(:,k)||^2 = G(k,k).  A zero
+ * denominator (the paper does not treat it) leaves the row unchanged. */
+void orc_hals_row_h(int64_t n, int r, const double *A, const double *G,
+                    double *H, int k)
+{
+    const double gkk = G[k * r + k];
+    if (!(gkk > 0.0)) return;
+    for (int64_t c = 0; c < n; ++c) {
+        double s = A[k * n + c];
+        for (int j = 0; j < r; ++j) {
+            if (j == k) continue;
+            s -= G[k * r + j] * H[j * n + c];
+        }
+        double v = s / gkk;
+        H[k * n + c] = v > 0.0 ? v : 0.0;
+    }
+}
+
+/* The same closed form for column k of W, from the symmetry
+ * ||X - WH|| = ||X^T - H^T W^T|| (Sec. 1):
+ *   W(:,k) = max(0, (X H(k,:)^T - sum_{j != k} W(:,j) (H(j,:) H(k,:)^T))
+ *                    / ||H(k,:)||^2)
+ * with C = X H^T and D = H H^T. */
+void orc_hals_col_w(int64_t m, int r, const double *C, const double *D,
+                    double *W, int k)
+{
+    const double dkk = D[k * r + k];
+    if (!(dkk > 0.0)) return;
+    for (int64_t i = 0; i < m; ++i) {
+        double s = C[i * r + k];
+        for (int j = 0; j < r; ++j) {
+            if (j == k) continue;
+            s -= W[i * r + j] * D[j * r + k];
+        }
+        double v = s / dkk;
+        W[i * r + k] = v > 0.0 ? v : 0.0;
+    }
+}
+
+/* A-HALS: the rows of H are updated in cyclic order, and the whole pass is
+ * repeated `sweeps` times reusing W^T W and W^T X (Sec. 1, second bullet). */
+void orc_hals_sweeps_h(int64_t n, int r, const double *A, const double *G,
+                       double *H, int sweeps)
+{
+    for (int l = 0; l < sweeps; ++l)
+        for (int k = 0; k < r; ++k) orc_hals_row_h(n, r, A, G, H, k);
+}
+
+void orc_hals_sweeps_w(int64_t m, int r, const double *C, const double *D,
+                       double *W, int sweeps)
+{
+    for (int l = 0; l < sweeps; ++l)
+        for (int k = 0; k < r; ++k) orc_hals_col_w(m, r, C, D, W, k);
+}
+
+/* Remark 1: ||X||^2 - 2 <W, X H^T> + <W^T W, H H^T>. */
+double orc_err2_expanded(double fro2, int64_t m, int r, const double *W,
+                         const double *C, const double *D)
+{
+    double cross = 0.0;
+    for (int64_t i = 0; i < m; ++i)
+        for (int k = 0; k < r; ++k) cross += W[i * r + k] * C[i * r + k];
+    double *G = orc_alloc((int64_t)r * r);
+    orc_gram_w(m, r, W, G);
+    double quad = 0.0;
+    for (int k = 0; k < r; ++k)
+        for (int j = 0; j < r; ++j) quad += G[k * r + j] * D[k * r + j];
+    free(G);
+    return fro2 - 2.0 * cross + quad;
+}
+
+/* sum_{i,j} (X(i,j) - (WH)(i,j))^2, every entry formed explicitly. */
+double orc_err2_direct(const orc_matrix *X, int r, const double *W,
+                       const double *H)
+{
+    const int64_t m = X->m, n = X->n;
+    double *row = orc_alloc(n);
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            double wh = 0.0;
+            for (int k = 0; k < r; ++k) wh += W[i * r + k] * H[k * n + j];
+            row[j] = -wh;
+        }
+        if (X->is_csr) {
+            for (int64_t p = X->rowptr[i]; p < X->rowptr[i + 1]; ++p)
+                row[X->colidx[p]] += X->val[p];
+        } else {
+            for (int64_t j = 0; j < n; ++j) row[j] += X->x[i * n + j];
+        }
+        for (int64_t j = 0; j < n; ++j) s += row[j] * row[j];
+    }
+    free(row);
+    return s;
+}
+
+void orc_sweep_counts(int64_t m, int64_t n, int64_t K, int r, double alpha,
+                      int *lw, int *lh)
+{
+    double rho_w = 1.0 + ((double)K + (double)n * r) / ((double)m * (r + 1));
+    double rho_h = 1.0 + ((double)K + (double)m * r) / ((double)n * (r + 1));
+    *lw = (int)floor(1.0 + alpha * rho_w);
+    *lh = (int)floor(1.0 + alpha * rho_h);
+}
+
+/* Algorithm 3.  On decrease: beta_{k+1} = min(beta_bar, gamma beta_k), then
+ * beta_bar = min(1, gamma_bar beta_bar).  Otherwise: beta_{k+1} =
+ * beta_k / eta and beta_bar = beta_{k-1}. */
+void orc_beta_update(const orc_params *p, orc_scalars *s, int decreased)
+{
+    double next;
+    if (decreased) {
+        double grown = p->gamma * s->beta;
+        next = grown < s->beta_bar ? grown : s->beta_bar;
+        double bar = p->gamma_bar * s->beta_bar;
+        s->beta_bar = bar < 1.0 ? bar : 1.0;
+    } else {
+        next = s->beta / p->eta;
+        s->beta_bar = s->beta_prev;
+    }
+    s->beta_prev = s->beta;
+    s->beta = next;
+}
+
+void orc_eahals_init(const orc_matrix *X, int r, const double *W,
+                     const double *H, double *Wy, double *Hy,
+                     const orc_params *p, orc_scalars *s)
+{
+    const int64_t m = X->m, n = X->n;
+    memcpy(Wy, W, sizeof(double) * (size_t)(m * r));
+    memcpy(Hy, H, sizeof(double) * (size_t)(r * n));
+    double fro2 = orc_fro2(X);
+    double *C = orc_alloc(m * r), *D = orc_alloc((int64_t)r * r);
+    orc_xht(X, r, H, C);
+    orc_gram_h(n, r, H, D);
+    double e2 = orc_err2_expanded(fro2, m, r, W, C, D);
+    free(C);
+    free(D);
+    double e0 = sqrt(e2 > 0.0 ? e2 : 0.0);
+    s->beta = p->beta0;
+    s->beta_bar = 1.0;
+    s->beta_prev = p->beta0;
+    s->e_last = e0;
+    s->e_prev = e0;
+    s->k = 0;
+}
+
+/* One outer iteration of Algorithm 2 (steps 3 to 20) plus Algorithm 3. */
+void orc_eahals_step(const orc_matrix *X, int r, double fro2, double *W,
+                     double *H, double *Wy, double *Hy, const orc_params *p,
+                     orc_scalars *s, int force, double *e_out,
+                     double *beta_out, int *accepted_out)
+{
+    const int64_t m = X->m, n = X->n;
+    const double beta = s->beta;
+    double *A = orc_alloc(r * n), *G = orc_alloc((int64_t)r * r);
+    double *C = orc_alloc(m * r), *D = orc_alloc((int64_t)r * r);
+    double *Hn = orc_alloc(r * n), *Wn = orc_alloc(m * r);
+    double *Hw = orc_alloc(r * n);     /* the H that the W-update sees */
+    double *Wy_new = orc_alloc(m * r), *Hy_new = orc_alloc(r * n);
+
+    /* Step 3: H_n from NNLS on ||X - W_y H_n|| warm-started at H_y. */
+    orc_wtx(X, r, Wy, A);
+    orc_gram_w(m, r, Wy, G);
+    memcpy(Hn, Hy, sizeof(double) * (size_t)(r * n));
+    orc_hals_sweeps_h(n, r, A, G, Hn, p->lh);
+
+    /* Steps 4-9: for hp >= 2, H_y = H_n + beta (H_n - H), projected when
+     * hp = 3.  For hp = 1 the W-update uses H_n (H is extrapolated only
+     * after it, as a warm start for the next H-update). */
+    for (int64_t q = 0; q < r * n; ++q) {
+        if (p->hp >= 2) {
+            double v = Hn[q] + beta * (Hn[q] - H[q]);
+            if (p->hp == 3) v = v > 0.0 ? v : 0.0;
+            Hw[q] = v;
+        } else {
+            Hw[q] = Hn[q];
+        }
+    }
+
+    /* Step 10: W_n from NNLS on ||X - W_n H_y|| warm-started at W_y. */
+    orc_xht(X, r, Hw, C);
+    orc_gram_h(n, r, Hw, D);
+    memcpy(Wn, Wy, sizeof(double) * (size_t)(m * r));
+    orc_hals_sweeps_w(m, r, C, D, Wn, p->lw);
+
+    /* Step 15 via Remark 1, reusing X H_y^T and H_y H_y^T of step 10. */
+    double e2 = orc_err2_expanded(fro2, m, r, Wn, C, D);
+    double e = sqrt(e2 > 0.0 ? e2 : 0.0);
+
+    /* Step 11: W_y = W_n + beta (W_n - W); step 13 (hp = 1). */
+    for (int64_t q = 0; q < m * r; ++q) {
+        double v = Wn[q] + beta * (Wn[q] - W[q]);
+        if (p->project_w) v = v > 0.0 ? v : 0.0;
+        Wy_new[q] = v;
+    }
+    for (int64_t q = 0; q < r * n; ++q)
+        Hy_new[q] = (p->hp == 1) ? Hn[q] + beta * (Hn[q] - H[q]) : Hw[q];
+
+    /* Steps 16-20. */
+    double ref = p->compare_prev ? s->e_prev : s->e_last;
+    int accept = (force >= 0) ? (force != 0) : !(e > ref);
+    if (accept) {
+        memcpy(W, Wn, sizeof(double) * (size_t)(m * r));
+        memcpy(H, Hn, sizeof(double) * (size_t)(r * n));
+        memcpy(Wy, Wy_new, sizeof(double) * (size_t)(m * r));
+        memcpy(Hy, Hy_new, sizeof(double) * (size_t)(r * n));
+        s->e_last = e;
+    } else {
+        memcpy(Wy, W, sizeof(double) * (size_t)(m * r));
+        memcpy(Hy, H, sizeof(double) * (size_t)(r * n));
+    }
+    s->e_prev = e;
+    orc_beta_update(p, s, accept);
+    s->k += 1;
+
+    if (e_out) *e_out = e;
+    if (beta_out) *beta_out = beta;
+    if (accepted_out) *accepted_out = accept;
+    free(A); free(G); free(C); free(D); free(Hn); free(Wn); free(Hw);
+    free(Wy_new); free(Hy_new);
+}
+
+void orc_eahals_run(const orc_matrix *X, int r, double *W, double *H,
+                    double *Wy, double *Hy, const orc_params *p,
+                    orc_scalars *s, int iters, const int8_t *forced,
+                    double *trace_e, double *trace_beta, uint8_t *trace_acc)
+{
+    double fro2 = orc_fro2(X);
+    for (int it = 0; it < iters; ++it) {
+        double e, b;
+        int acc;
+        orc_eahals_step(X, r, fro2, W, H, Wy, Hy, p, s,
+                        forced ? forced[it] : -1, &e, &b, &acc);
+        if (trace_e) trace_e[it] = e;
+        if (trace_beta) trace_beta[it] = b;
+        if (trace_acc) trace_acc[it] = (uint8_t)acc;
+    }
+}
+
+void orc_ahals_run(const orc_matrix *X, int r, double *W, double *H,
+                   int lw, int lh, int iters, double *trace_e)
+{
+    const int64_t m = X->m, n = X->n;
+    double fro2 = orc_fro2(X);
+    double *A = orc_alloc(r * n), *G = orc_alloc((int64_t)r * r);
+    double *C = orc_alloc(m * r), *D = orc_alloc((int64_t)r * r);
+    for (int it = 0; it < iters; ++it) {
+        orc_wtx(X, r, W, A);
+        orc_gram_w(m, r, W, G);
+        orc_hals_sweeps_h(n, r, A, G, H, lh);
+        orc_xht(X, r, H, C);
+        orc_gram_h(n, r, H, D);
+        orc_hals_sweeps_w(m, r, C, D, W, lw);
+        if (trace_e) {
+            double e2 = orc_err2_expanded(fro2, m, r, W, C, D);
+            trace_e[it] = sqrt(e2 > 0.0 ? e2 : 0.0);
+        }
+    }
+    free(A); free(G); free(C); free(D);
+}

@@ -1,0 +1,418 @@
+"""Pins for the FP64 oracle: each routine is checked against something other
+than itself -- a library routine it reduces to, brute force on tiny inputs, a
+closed form, an invariant the paper states, or a hand-derived example.
+
+Which pin covers which oracle routine:
+  orc_fro2, orc_wtx, orc_xht, orc_gram_*   numpy / scipy products (library)
+  orc_hals_row_h, orc_hals_col_w           1-D brute-force minimisation of the
+                                           direct objective (Sec. 1 closed form)
+  orc_hals_sweeps_*                        convergence to brute-force NNLS
+                                           (all 2^r active sets), monotone decrease
+  orc_err2_expanded / orc_err2_direct      Remark 1 identity + numpy direct error
+  orc_sweep_counts                         hand-evaluated budgets
+  orc_beta_update                          hand-derived Algorithm 3 sequences
+  orc_eahals_*                             hand-worked 2x2 example, beta0 = 0
+                                           reduces to A-HALS, accepted errors
+                                           monotone, hp=3 feasibility, exact
+                                           power-of-two scaling equivariance,
+                                           low-rank recovery, KKT, acceleration
+                                           over A-HALS (Table 3's claim)
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_1805_06604_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand(shape, seed):
+    return wl.rng(seed).random(shape)
+
+
+def _csr(X):
+    rp, ci, v = wl.csr_from_dense(X)
+    return O.Matrix(m=X.shape[0], n=X.shape[1], rowptr=rp, colidx=ci, val=v)
+
+
+def _sparse_dense(m, n, density, seed):
+    g = wl.rng(seed)
+    X = g.random((m, n)) * (g.random((m, n)) < density)
+    X[3, :] = 0.0            # an empty row
+    return X
+
+
+# ---------------------------------------------------------------- products
+
+@pytest.mark.parametrize("m,n,r", [(7, 5, 3), (37, 23, 6), (64, 41, 17)])
+def test_products_match_numpy(m, n, r):
+    X = _rand((m, n), 1) - 0.3        # X may be negative (X in R^{m x n})
+    W = _rand((m, r), 2)
+    H = _rand((r, n), 3)
+    np.testing.assert_allclose(O.wtx(X, W), W.T @ X, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(O.xht(X, H), X @ H.T, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(O.gram_w(W), W.T @ W, rtol=1e-13)
+    np.testing.assert_allclose(O.gram_h(H), H @ H.T, rtol=1e-13)
+    assert O.fro2(X) == pytest.approx(np.linalg.norm(X) ** 2, rel=1e-14)
+
+
+def test_csr_products_match_scipy():
+    X = _sparse_dense(53, 31, 0.1, 4)
+    S = sp.csr_matrix(X)
+    W = _rand((53, 5), 5)
+    H = _rand((5, 31), 6)
+    M = _csr(X)
+    np.testing.assert_allclose(O.wtx(M, W), (S.T @ W).T, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(O.xht(M, H), S @ H.T, rtol=1e-13, atol=1e-14)
+    assert O.fro2(M) == pytest.approx(sp.linalg.norm(S) ** 2, rel=1e-14)
+    assert O.err2_direct(M, W, H) == pytest.approx(np.linalg.norm(X - W @ H) ** 2, rel=1e-12)
+
+
+# ---------------------------------------------------------------- Remark 1
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_expanded_error_equals_direct(seed):
+    m, n, r = 31, 19, 4
+    X = _rand((m, n), seed) * 3 - 1
+    W = _rand((m, r), seed + 10)
+    H = _rand((r, n), seed + 20)
+    direct = np.linalg.norm(X - W @ H) ** 2            # library, independent
+    assert O.err2_direct(X, W, H) == pytest.approx(direct, rel=1e-12)
+    C = X @ H.T
+    D = H @ H.T
+    assert O.err2_expanded(O.fro2(X), W, C, D) == pytest.approx(direct, rel=1e-12)
+
+
+# ------------------------------------------------------- HALS closed form
+
+def _objective(X, W, H):
+    return float(np.sum((X - W @ H) ** 2))
+
+
+def _argmin_1d(f, hi):
+    """Minimise a convex scalar f on [0, hi] by grid + golden section."""
+    ts = np.linspace(0.0, hi, 2001)
+    vals = np.array([f(t) for t in ts])
+    i = int(np.argmin(vals))
+    a, b = ts[max(i - 1, 0)], ts[min(i + 1, len(ts) - 1)]
+    phi = (np.sqrt(5) - 1) / 2
+    for _ in range(200):
+        c, d = b - phi * (b - a), a + phi * (b - a)
+        if f(c) <= f(d):
+            b = d
+        else:
+            a = c
+    return 0.5 * (a + b)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_row_update_is_exact_1d_minimiser(k):
+    """Sec. 1: the closed form is argmin over H(k,:) >= 0 of ||X - WH||^2."""
+    m, n, r = 9, 6, 3
+    X = _rand((m, n), 7) * 2 - 0.5
+    W = _rand((m, r), 8)
+    H = _rand((r, n), 9)
+    Hn = O.hals_row_h(W.T @ X, W.T @ W, H, k)
+    assert np.all(Hn[k] >= 0)
+    others = [i for i in range(r) if i != k]
+    np.testing.assert_array_equal(Hn[others], H[others])
+    for j in range(n):
+        def f(t, j=j):
+            h = H[:, j].copy()
+            h[k] = t
+            return float(np.sum((X[:, j] - W @ h) ** 2))
+        t_star = _argmin_1d(f, 10.0)
+        assert Hn[k, j] == pytest.approx(t_star, abs=1e-7)
+    assert _objective(X, W, Hn) <= _objective(X, W, H) + 1e-12
+
+
+@pytest.mark.parametrize("k", [0, 2])
+def test_col_update_is_exact_1d_minimiser(k):
+    m, n, r = 7, 10, 3
+    X = _rand((m, n), 11) * 2 - 0.5
+    W = _rand((m, r), 12)
+    H = _rand((r, n), 13)
+    Wn = O.hals_col_w(X @ H.T, H @ H.T, W, k)
+    assert np.all(Wn[:, k] >= 0)
+    for i in range(m):
+        def f(t, i=i):
+            w = W[i].copy()
+            w[k] = t
+            return float(np.sum((X[i] - w @ H) ** 2))
+        assert Wn[i, k] == pytest.approx(_argmin_1d(f, 10.0), abs=1e-7)
+
+
+def test_zero_denominator_leaves_row_unchanged():
+    m, n, r = 6, 5, 3
+    X = _rand((m, n), 14)
+    W = _rand((m, r), 15)
+    W[:, 1] = 0.0
+    H = _rand((r, n), 16)
+    Hn = O.hals_row_h(W.T @ X, W.T @ W, H, 1)
+    np.testing.assert_array_equal(Hn, H)
+
+
+def _nnls_bruteforce(W, x):
+    """Exact min_{h>=0} ||x - W h|| by enumerating every passive set."""
+    r = W.shape[1]
+    best, best_h = np.inf, None
+    for mask in itertools.product([0, 1], repeat=r):
+        S = [i for i in range(r) if mask[i]]
+        h = np.zeros(r)
+        if S:
+            sol, *_ = np.linalg.lstsq(W[:, S], x, rcond=None)
+            if np.any(sol < 0):
+                continue
+            h[S] = sol
+        v = float(np.sum((x - W @ h) ** 2))
+        if v < best:
+            best, best_h = v, h
+    return best_h
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_sweeps_converge_to_bruteforce_nnls(r):
+    m, n = 12, 8
+    X = _rand((m, n), 20 + r) * 2 - 0.6
+    W = _rand((m, r), 30 + r) + 0.05
+    H0 = _rand((r, n), 40 + r)
+    H = O.hals_sweeps_h(W.T @ X, W.T @ W, H0, 3000)
+    for j in range(n):
+        np.testing.assert_allclose(H[:, j], _nnls_bruteforce(W, X[:, j]), atol=1e-9)
+    # and the W side through the transposed problem
+    Ht = _rand((r, m), 50 + r) + 0.05
+    W0 = _rand((n, r), 60 + r)
+    Wn = O.hals_sweeps_w(X.T @ Ht.T, Ht @ Ht.T, W0, 3000)
+    for i in range(n):
+        np.testing.assert_allclose(Wn[i], _nnls_bruteforce(Ht.T, X[:, i]), atol=1e-9)
+
+
+def test_every_row_update_decreases_objective():
+    """HALS is an exact block coordinate descent: no single update can
+    increase ||X - WH||^2 (Sec. 1)."""
+    m, n, r = 20, 15, 5
+    X = _rand((m, n), 70)
+    W = _rand((m, r), 71)
+    H = _rand((r, n), 72)
+    f = _objective(X, W, H)
+    for sweep in range(4):
+        A, G = W.T @ X, W.T @ W
+        for k in range(r):
+            H = O.hals_row_h(A, G, H, k)
+            f2 = _objective(X, W, H)
+            assert f2 <= f * (1 + 1e-14)
+            f = f2
+        C, D = X @ H.T, H @ H.T
+        for k in range(r):
+            W = O.hals_col_w(C, D, W, k)
+            f2 = _objective(X, W, H)
+            assert f2 <= f * (1 + 1e-14)
+            f = f2
+
+
+# -------------------------------------------------------- sweep budget
+
+def test_sweep_counts_hand_evaluated():
+    # rho_W = 1 + (K + n r)/(m (r+1)), L = floor(1 + 0.5 rho)
+    # 200x150 r=10: rho_W = 1 + 31500/2200 = 15.32 -> 8; rho_H = 1 + 32000/1650 = 20.39 -> 11
+    assert O.sweep_counts(200, 150, 200 * 150, 10) == (8, 11)
+    # 10000x4000 r=50: rho_W = 79.82 -> 40; rho_H = 199.5 -> 100
+    assert O.sweep_counts(10000, 4000, 10000 * 4000, 50) == (40, 100)
+    # 10304x4000 r=64: rho_W = 1 + 41472000/669760 = 62.9 -> 32; rho_H = 1 + 41875456/260000 = 162.06 -> 82
+    assert O.sweep_counts(10304, 4000, 10304 * 4000, 64) == (32, 82)
+    # 50000x20000 r=30, K=3e6: rho_W = 3.32 -> 2; rho_H = 8.26 -> 5
+    assert O.sweep_counts(50000, 20000, 3_000_000, 30) == (2, 5)
+
+
+# -------------------------------------------------------- Algorithm 3
+
+def test_beta_update_hand_derived():
+    with open(os.path.join(GOLDEN, "beta_update_alg3.json")) as f:
+        gold = json.load(f)
+    for case in gold["cases"]:
+        pr = case["params"]
+        p = O.Params(beta0=pr["beta0"], gamma=pr["gamma"], gamma_bar=pr["gamma_bar"], eta=pr["eta"])
+        s = O.Scalars(beta=pr["beta0"], beta_bar=1.0, beta_prev=pr["beta0"])
+        for t, d in enumerate(case["decisions"]):
+            s = O.beta_update(p, s, bool(d))
+            assert s.beta == pytest.approx(case["beta"][t], rel=1e-15)
+            assert s.beta_bar == pytest.approx(case["beta_bar"][t], rel=1e-15)
+            assert s.beta_prev == pytest.approx(case["beta_prev"][t], rel=1e-15)
+
+
+def test_beta_zero_stays_zero():
+    """beta_k = 0 for all k gives back the original algorithm (Sec. 2)."""
+    p = O.Params(beta0=0.0)
+    s = O.Scalars(beta=0.0, beta_bar=1.0, beta_prev=0.0)
+    for d in [1, 0, 1, 1, 0]:
+        s = O.beta_update(p, s, bool(d))
+        assert s.beta == 0.0
+
+
+# -------------------------------------------------------- Algorithm 2
+
+def test_worked_example_2x2_rank1():
+    with open(os.path.join(GOLDEN, "worked_example_2x2_r1.json")) as f:
+        g = json.load(f)
+    pr = g["problem"]
+    X = np.array(pr["X"])
+    p = O.Params(hp=pr["hp"], beta0=pr["beta0"], eta=pr["eta"], gamma=pr["gamma"],
+                 gamma_bar=pr["gamma_bar"], lw=pr["lw"], lh=pr["lh"])
+    st = O.eahals_init(X, np.array(pr["W0"]), np.array(pr["H0"]), p)
+    assert st.s.e_last == pytest.approx(g["e0"], rel=1e-14)
+    te, tb, ta = O.eahals_run(X, st, p, 2)
+    np.testing.assert_allclose(te, g["e"], rtol=1e-12)
+    np.testing.assert_allclose(tb, g["beta_used"], rtol=1e-15)
+    np.testing.assert_array_equal(ta, np.array(g["accepted"], dtype=bool))
+    fin = g["final"]
+    for name in ("W", "H", "Wy", "Hy"):
+        np.testing.assert_allclose(getattr(st, name), np.array(fin[name]), rtol=1e-12, atol=1e-14)
+    assert st.s.beta == pytest.approx(fin["beta"], rel=1e-15)
+    assert st.s.beta_bar == pytest.approx(fin["beta_bar"], rel=1e-15)
+    assert st.s.beta_prev == pytest.approx(fin["beta_prev"], rel=1e-15)
+
+
+@pytest.mark.parametrize("hp", [1, 2, 3])
+def test_beta0_zero_is_ahals(hp):
+    P = wl.low_rank(40, 30, 5, seed=3, noise=0.05, dtype=np.float64)
+    p = O.Params(hp=hp, beta0=0.0, lw=3, lh=4)
+    st = O.eahals_init(P.X, P.W0, P.H0, p)
+    te, tb, ta = O.eahals_run(P.X, st, p, 40)
+    assert ta.all()
+    W, H, tea = O.ahals_run(P.X, P.W0, P.H0, 3, 4, 40)
+    np.testing.assert_array_equal(st.W, W)
+    np.testing.assert_array_equal(st.H, H)
+    np.testing.assert_array_equal(te, tea)
+
+
+@pytest.mark.parametrize("hp,compare_prev", [(1, 0), (2, 0), (3, 0), (3, 1)])
+def test_restart_logic_and_accepted_errors(hp, compare_prev):
+    P = wl.low_rank(60, 45, 6, seed=5, noise=0.02, dtype=np.float64)
+    p = O.Params(hp=hp, beta0=0.75, eta=1.5, gamma=1.1, gamma_bar=1.05, lw=2, lh=3,
+                 compare_prev=compare_prev)
+    st = O.eahals_init(P.X, P.W0, P.H0, p)
+    e0 = st.s.e_last
+    te, tb, ta = O.eahals_run(P.X, st, p, 120)
+    assert (~ta).any(), "aggressive parameters should trigger at least one restart"
+    ref, prev = e0, e0
+    for e, a in zip(te, ta):
+        cmp = prev if compare_prev else ref
+        assert a == (not e > cmp)
+        if a:
+            ref = e
+        prev = e
+    if not compare_prev:
+        acc = np.concatenate([[e0], te[ta]])
+        assert np.all(np.diff(acc) <= 0.0)
+
+
+def test_hp3_keeps_extrapolated_h_feasible_and_error_is_of_feasible_pair():
+    """hp = 3 projects H_y, so (W_n, H_y) is feasible (Sec. 2)."""
+    P = wl.low_rank(50, 40, 5, seed=8, noise=0.0, dtype=np.float64)
+    p = O.Params(hp=3, lw=3, lh=3)
+    st = O.eahals_init(P.X, P.W0, P.H0, p)
+    for _ in range(30):
+        O.eahals_step(P.X, st, p)
+        assert np.all(st.Hy >= 0)
+        assert np.all(st.H >= 0) and np.all(st.W >= 0)
+
+
+def test_hp1_error_is_of_wn_hn():
+    """For hp = 1 the W-update and e(k) use H_n (H is extrapolated after)."""
+    P = wl.low_rank(30, 25, 4, seed=9, noise=0.05, dtype=np.float64)
+    p = O.Params(hp=1, lw=2, lh=2)
+    st = O.eahals_init(P.X, P.W0, P.H0, p)
+    for _ in range(10):
+        e, _, acc = O.eahals_step(P.X, st, p)
+        if acc:
+            assert e == pytest.approx(np.linalg.norm(P.X - st.W @ st.H), rel=1e-9)
+
+
+def test_power_of_two_scaling_equivariance_is_exact():
+    """W -> W L, H -> L^-1 H leaves WH unchanged; every step of Algorithm 2 is
+    equivariant, and power-of-two scalings make it exact in floating point."""
+    P = wl.low_rank(40, 35, 4, seed=10, noise=0.05, dtype=np.float64)
+    lam = np.array([2.0, 0.25, 8.0, 0.5])
+    p = O.Params(hp=3, lw=3, lh=4)
+    st1 = O.eahals_init(P.X, P.W0, P.H0, p)
+    st2 = O.eahals_init(P.X, P.W0 * lam, P.H0 / lam[:, None], p)
+    te1, _, ta1 = O.eahals_run(P.X, st1, p, 25)
+    te2, _, ta2 = O.eahals_run(P.X, st2, p, 25)
+    np.testing.assert_array_equal(ta1, ta2)
+    np.testing.assert_allclose(te1, te2, rtol=1e-13)
+    np.testing.assert_allclose(st2.W, st1.W * lam, rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(st2.H, st1.H / lam[:, None], rtol=1e-12, atol=1e-300)
+
+
+def test_csr_and_dense_give_the_same_iterates():
+    X = _sparse_dense(40, 30, 0.3, 11)
+    W0, H0 = wl.init_factors(40, 30, 4, 12, np.float64)
+    p = O.Params(hp=3, lw=2, lh=3)
+    st1 = O.eahals_init(X, W0, H0, p)
+    st2 = O.eahals_init(_csr(X), W0, H0, p)
+    te1, _, ta1 = O.eahals_run(X, st1, p, 15)
+    te2, _, ta2 = O.eahals_run(_csr(X), st2, p, 15)
+    np.testing.assert_array_equal(ta1, ta2)
+    np.testing.assert_allclose(te1, te2, rtol=1e-10)
+    np.testing.assert_allclose(st1.W, st2.W, rtol=1e-9, atol=1e-12)
+
+
+def test_extrapolation_accelerates_ahals_on_low_rank():
+    """Table 3 / Fig. 3: on exactly low-rank synthetic data E-A-HALS (hp=3,
+    beta0=.5, eta=1.5, gamma=1.01, gamma_bar=1.005) ends far below A-HALS
+    after the same number of outer iterations."""
+    wins = 0
+    for seed in range(3):
+        P = wl.low_rank(100, 80, 8, seed=100 + seed, dtype=np.float64)
+        lw, lh = O.sweep_counts(P.m, P.n, P.nnz, P.r)
+        nrm = np.sqrt(O.fro2(P.X))
+        p = O.Params(hp=3, lw=lw, lh=lh)
+        st = O.eahals_init(P.X, P.W0, P.H0, p)
+        O.eahals_run(P.X, st, p, 150)
+        e_ext = np.linalg.norm(P.X - st.W @ st.H) / nrm
+        W, H, _ = O.ahals_run(P.X, P.W0, P.H0, lw, lh, 150)
+        e_plain = np.linalg.norm(P.X - W @ H) / nrm
+        wins += e_ext < 0.5 * e_plain
+    assert wins == 3
+
+
+@pytest.mark.slow
+def test_low_rank_recovery_and_kkt():
+    """X = W0 H0 admits zero error (e_min = 0, Sec. 4.2); E-A-HALS drives the
+    relative error and the KKT residuals of (1) towards zero."""
+    P = wl.oracle_scale(0)
+    lw, lh = O.sweep_counts(P.m, P.n, P.nnz, P.r)
+    p = O.Params(hp=3, lw=lw, lh=lh)
+    st = O.eahals_init(P.X, P.W0, P.H0, p)
+    X = P.X
+
+    def kkt(W, H):
+        gW = 2 * (W @ (H @ H.T) - X @ H.T)      # gradient, Remark 1
+        gH = 2 * ((W.T @ W) @ H - W.T @ X)
+        return np.linalg.norm(np.minimum(W, gW)) + np.linalg.norm(np.minimum(H, gH))
+
+    k0 = kkt(st.W, st.H)
+    O.eahals_run(X, st, p, 3000)
+    rel = np.linalg.norm(X - st.W @ st.H) / np.linalg.norm(X)
+    assert rel < 1e-6
+    assert kkt(st.W, st.H) < 1e-6 * k0
+
+
+def test_tie_is_accepted():
+    """Algorithm 2 restarts only when e(k) > e(k-1): an exact fixed point
+    (X = [1], W = H = [1], every quantity exact in binary) ties at e = 0 and
+    must keep accepting, so beta grows as on a decrease (Algorithm 3)."""
+    X = np.array([[1.0]])
+    p = O.Params(hp=3, lw=1, lh=1)
+    st = O.eahals_init(X, np.array([[1.0]]), np.array([[1.0]]), p)
+    assert st.s.e_last == 0.0
+    te, tb, ta = O.eahals_run(X, st, p, 3)
+    np.testing.assert_array_equal(te, [0.0, 0.0, 0.0])
+    assert ta.all()
+    np.testing.assert_allclose(tb, [0.5, 0.505, 0.51005], rtol=1e-15)
