@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Throughput of the E-A-HALS outer loop on GB300 (one JSON line on stdout).
+
+A step is one outer iteration of Algorithm 2 (all kernels of the hot path:
+Grams, W^T X, H sweeps + extrapolation, X H^T, W sweeps + error + restart
+decision + Algorithm 3, finalize) on the dense noisy low-rank workload
+m = 10000, n = 4000, r = 50 (FP32 path, paper defaults hp = 3, beta0 = 0.5,
+eta = 1.5, gamma = 1.01, gamma_bar = 1.005, A-HALS sweep budget L_W = 40,
+L_H = 100).  X (160 MB) is larger than the 129 MB L2, so no flush is needed
+between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own instance (independent problems, no
+collective on the data path, weak scaling); the timed region is bracketed by
+a barrier and synchronisation and the slowest rank's time is used.
+``--impl reference`` times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "E-A-HALS outer iters/s & time-to-rel-err on 1 GB300; % of HBM roofline"
+UNIT = "iter/s"
+WORKLOAD = "dense_noisy_10000x4000_r50"
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip e2e / time-to-target / phase profile (quick runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.out.read())) if len(r) >= 9]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(seed: int):
+    from paper_1805_06604_gb300 import workloads as wl
+    return wl.dense_noisy(seed)
+
+
+def phase_work(P, lw, lh):
+    """Algorithmic (flops, bytes) of one launch of every phase (FP32 data)."""
+    m, n, r = P.m, P.n, P.r
+    f4 = 4
+    return {
+        "gram_w": (2 * m * r * r, f4 * m * r),
+        "wtx": (2 * m * n * r, f4 * (m * n + m * r + r * n)),
+        "hals_h": (2 * r * r * lh * n, f4 * 5 * r * n),
+        "gram_h": (2 * n * r * r, f4 * r * n),
+        "xht": (2 * m * n * r, f4 * (m * n + r * n + m * r)),
+        "hals_w": (2 * r * r * (lw + 1) * m, f4 * 3 * m * r),
+        "finalize": (0, f4 * 4 * (m * r + r * n)),
+    }
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for rel in ent.get("sources", []):
+        p = os.path.join(ROOT, rel)
+        if not os.path.exists(p):
+            return None
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != ent.get("digest"):
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def cpu_baseline_oracle(P, lw, lh, iters: int):
+    import numpy as np
+    import oracle as O
+    O.build()
+    p = O.Params(hp=3, lw=lw, lh=lh)
+    X = O.Matrix(P.X.astype(np.float64))
+    st = O.eahals_init(X, P.W0, P.H0, p)
+    f2 = O.fro2(X)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        O.eahals_step(X, st, p, fro2_x=f2)
+    dt = time.perf_counter() - t0
+    return iters / dt, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    from paper_1805_06604_gb300 import nmf as _unused  # noqa: F401  (package importable)
+    import numpy as np
+    import oracle as O
+    O.build()
+    P = make_workload(args.seed)
+    lw, lh = O.sweep_counts(P.m, P.n, P.nnz, P.r)
+    p = O.Params(hp=3, lw=lw, lh=lh)
+    X = O.Matrix(P.X.astype(np.float64))
+    st = O.eahals_init(X, P.W0, P.H0, p)
+    f2 = O.fro2(X)
+    warm = min(args.warmup, 1)
+    t0 = time.perf_counter()
+    for _ in range(max(warm, 1)):
+        O.eahals_step(X, st, p, fro2_x=f2)
+    per = time.perf_counter() - t0
+    budget = 150.0
+    steps = max(1, min(args.steps, int(budget / max(per, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        O.eahals_step(X, st, p, fro2_x=f2)
+    dt = time.perf_counter() - t0
+    value = steps / dt
+    sample = (f"{steps} full outer iterations of {WORKLOAD} (FP64 oracle, one thread), "
+              f"after {max(warm, 1)} untimed; steps capped to keep the run near {budget:.0f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": steps, "steps_requested": args.steps, "warmup": max(warm, 1),
+            "ms_per_step": 1000.0 * dt / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": P.m, "n": P.n, "r": P.r, "lw": lw, "lh": lh,
+                       "hp": 3, "beta0": 0.5, "eta": 1.5, "gamma": 1.01, "gamma_bar": 1.005},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    return line
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1805_06604_gb300 import build as nb
+    from paper_1805_06604_gb300 import nmf
+
+    nb.build()
+    nmf.load()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    P = make_workload(args.seed + rank)
+    lw, lh = nmf.nmf_sweep_counts(P.m, P.n, P.nnz, P.r)
+    stream = torch.cuda.current_stream()
+    Xd = torch.from_numpy(P.X).cuda()
+    W0d = torch.from_numpy(P.W0).cuda()
+    H0d = torch.from_numpy(P.H0).cuda()
+    solver = nmf.Solver(Xd, P.r, W0d, H0d, stream=stream)
+    solver.step(args.warmup)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    solver.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    t = e0.elapsed_time(e1) / 1000.0
+    if dist is not None:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    info = solver.info()
+    value = world * args.steps / t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": P.m, "n": P.n, "r": P.r, "lw": lw, "lh": lh,
+                       "hp": 3, "beta0": 0.5, "eta": 1.5, "gamma": 1.01, "gamma_bar": 1.005,
+                       "precision": "fp32", "parallelism": f"independent instance per GPU x{world}",
+                       "l2": "inputs larger than L2 (X is 160 MB), no flush"},
+            "clocks": clocks,
+            "gpu_launches": int(info.launches_per_iter) * args.steps,
+            "relerr_after_timed": info.relerr}
+    if rank != 0:
+        solver.close()
+        return None
+    if args.no_extras:
+        solver.close()
+        return line
+
+    hbm_gbs, sm_max_mhz, peak_src = peaks()
+    alu_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    # Per-phase device time: an event-instrumented pass over the same step.
+    prof_iters = min(max(args.steps // 10, 5), 50)
+    ms = solver.profile_phases(prof_iters)
+    work = phase_work(P, lw, lh)
+    phases = {}
+    for k, v in ms.items():
+        fl, by = work[k]
+        s = v / 1000.0
+        t_alu = fl / (alu_tflops * 1e12)
+        t_hbm = by / (hbm_gbs * 1e9)
+        phases[k] = {"us": 1000.0 * v, "gflop": fl / 1e9, "mb": by / 1e6,
+                     "bound": "alu" if t_alu >= t_hbm else "hbm",
+                     "frac": (max(t_alu, t_hbm) / s) if s > 0 else None}
+    dom = max(ms, key=ms.get)
+    fl, by = work[dom]
+    s = ms[dom] / 1000.0
+    if phases[dom]["bound"] == "alu":
+        achieved, peak, unit = fl / s / 1e12, alu_tflops, "TFLOP/s"
+    else:
+        achieved, peak, unit = by / s / 1e9, hbm_gbs, "GB/s"
+    line["roofline"] = {"kernel": dom, "bound": phases[dom]["bound"], "achieved": achieved,
+                        "peak": peak, "unit": unit, "frac": achieved / peak,
+                        "traffic": load_traffic(dom),
+                        "peak_source": (f"{peak_src} HBM copy {hbm_gbs} GB/s; FP32 FMA peak = "
+                                        f"152 SMs x 128 lanes x 2 x {sm_max_mhz:.0f} MHz"),
+                        "algorithmic_per_launch": {"flops": fl, "bytes": by},
+                        "profiled_iters": prof_iters}
+    # The X-streaming products against HBM (the metric's roofline).
+    xbytes = {k: work[k][1] for k in ("wtx", "xht")}
+    line["x_products_hbm"] = {k: {"gbs": xbytes[k] / (ms[k] / 1000.0) / 1e9,
+                                  "frac_of_hbm": xbytes[k] / (ms[k] / 1000.0) / 1e9 / hbm_gbs}
+                              for k in xbytes}
+    # Whole-iteration roofline: the slower of the X bytes at HBM bandwidth and
+    # all flops at the FP32 peak, against the measured step time.
+    it_bytes = 2 * 4 * P.m * P.n
+    it_flops = sum(w[0] for w in work.values())
+    bound_s = max(it_bytes / (hbm_gbs * 1e9), it_flops / (alu_tflops * 1e12))
+    line["iteration_roofline"] = {"bound_us": bound_s * 1e6, "frac": bound_s / (t / args.steps),
+                                  "x_bytes": it_bytes, "flops": it_flops}
+    line["phases"] = phases
+
+    # End to end through the public API from pinned host buffers: create
+    # (X, W0, H0 uploaded), `steps` iterations, factors read back.
+    Xh = torch.from_numpy(P.X).pin_memory()
+    W0h = torch.from_numpy(P.W0).pin_memory()
+    H0h = torch.from_numpy(P.H0).pin_memory()
+    Wout = torch.empty((P.m, P.r), dtype=torch.float32).pin_memory()
+    Hout = torch.empty((P.r, P.n), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s2 = nmf.Solver(Xh, P.r, W0h, H0h, stream=stream)
+    s2.step(args.steps)
+    nmf.nmf_get_factors(s2.h, Wout, Hout)
+    inf2 = s2.info()
+    t_e2e = time.perf_counter() - t0
+    s2.close()
+    h2d = 4 * (P.m * P.n + P.m * P.r + P.r * P.n)
+    d2h = 4 * (P.m * P.r + P.r * P.n) + 128
+    line["e2e"] = {"value": args.steps / t_e2e, "unit": UNIT,
+                   "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                   "seconds": t_e2e, "relerr": inf2.relerr,
+                   "includes": "nmf_create (upload, validation, ||X||^2, e(0), graph capture), "
+                               "nmf_step x steps, nmf_get_factors, nmf_get_info"}
+
+    # Time to a target relative error: E-A-HALS vs un-extrapolated A-HALS.
+    ref = nmf.Solver(Xd, P.r, W0d, H0d, stream=stream)
+    ref.step(500)
+    target = 1.001 * ref.info().relerr
+    ref.close()
+    ttt = {"target_relerr": target, "definition": "1.001 x E-A-HALS relerr after 500 iterations"}
+    for name, kw in (("eahals", {}), ("ahals", {"beta0": 0.0})):
+        sv = nmf.Solver(Xd, P.r, W0d, H0d, stream=stream, **kw)
+        torch.cuda.synchronize()
+        res = sv.solve(5000, target_relerr=target, check_every=10)
+        ttt[name] = {"seconds": res.seconds, "iters": res.iters, "reached": bool(res.reached),
+                     "relerr": res.relerr}
+        sv.close()
+    line["time_to_relerr"] = ttt
+    solver.close()
+
+    if world == 1 and not args.no_cpu_baseline:
+        cpu_iters = 2
+        v, dt = cpu_baseline_oracle(P, lw, lh, cpu_iters)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{cpu_iters} outer iterations of {WORKLOAD} "
+                                          f"(FP64 oracle, one thread, {dt:.1f} s)"}
+    return line
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_ours(args, world, rank, local)
+    if line is not None and rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * nmf.h -- C-ABI of the GB300 E-A-HALS library (libnmf_gb300.so).
+ *
+ * Solves  min ||X - WH||_F^2  s.t. W >= 0, H >= 0                 (Eq. 1)
+ * with X in R^{m x n}, W in R^{m x r}, H in R^{r x n}, by the extrapolated
+ * accelerated HALS method of Ang & Gillis, "Accelerating Nonnegative Matrix
+ * Factorization Algorithms using Extrapolation" (arXiv 1805.06604):
+ * Algorithm 2 (extrapolation with restarts, variants hp = 1, 2, 3), the beta
+ * schedule of Algorithm 3, A-HALS inner loops built on the closed-form row
+ * update of Sec. 1, and the cheap error of Remark 1.
+ *
+ * Conventions for every call:
+ *  - Matrices are row-major FP32: X is m x n (leading dimension ld >= n) or
+ *    CSR; W is m x r (W[i*r+k]); H is r x n (H[k*n+j]).
+ *  - A pointer argument marked "host or device" is read according to the
+ *    accompanying on_device / to_device flag.  The library never keeps or
+ *    frees a caller's pointer: X, W0 and H0 are copied into library-owned
+ *    device buffers during nmf_create.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work of a handle is enqueued on the stream given
+ *    at creation; calls that return host data synchronise that stream.
+ *  - Every call returns an nmf_status; no C++ exception crosses the ABI and
+ *    no call exits the process.  nmf_last_error() gives a message for the
+ *    last failing call on the calling thread.
+ *  - The library runs only on sm_103a (GB300).  There is no CPU fallback:
+ *    without a usable CUDA device, nmf_create returns NMF_ECUDA.
+ */
+#ifndef NMF_GB300_H
+#define NMF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NMF_OK = 0,
+    NMF_EINVAL = 1,      /* bad argument (shape, pointer, parameter range)   */
+    NMF_ENOMEM = 2,      /* device or host allocation failed                  */
+    NMF_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed       */
+    NMF_ENONFINITE = 4,  /* NaN/Inf in the input or in the error e(k)         */
+    NMF_ETIMEOUT = 5,    /* a bounded device-side wait expired                */
+    NMF_ENOTSUP = 6      /* valid request outside this build (e.g. r > 128)  */
+} nmf_status;
+
+typedef enum { NMF_DENSE = 0, NMF_CSR = 1 } nmf_format;
+
+/* Arithmetic of the two X products (W^T X and X H^T).  Grams, sweeps and
+ * extrapolation are FP32 in every mode; the error terms are accumulated in
+ * FP64 (Remark 1). */
+typedef enum {
+    NMF_PREC_FP32 = 0,   /* FP32 FMA on CUDA cores                            */
+    NMF_PREC_TF32 = 1,   /* TF32 tensor cores (tcgen05), FP32 accumulate      */
+    NMF_PREC_BF16X3 = 2  /* split BF16 (hi/lo pair of X and of the factor),
+                            three tcgen05 products, FP32 accumulate           */
+} nmf_precision;
+
+typedef struct {
+    int32_t format;          /* nmf_format                                    */
+    int32_t on_device;       /* 1: pointers below are device memory; 0: host  */
+    int64_t m, n;            /* rows, columns                                 */
+    int64_t ld;              /* dense: row stride in elements (>= n); 0 = n   */
+    int64_t nnz;             /* CSR: number of stored entries                 */
+    const float *values;     /* dense m x ld, or CSR values[nnz]              */
+    const int64_t *rowptr;   /* CSR: m+1 offsets, rowptr[0] = 0, nondecreasing */
+    const int32_t *colidx;   /* CSR: nnz column indices in [0, n)             */
+} nmf_matrix;
+
+typedef struct {
+    int32_t hp;              /* Algorithm 2 variant: 1, 2 or 3 (default 3)    */
+    double beta0;            /* Algorithm 3 initial beta, in [0, 1] (0.5).
+                                beta0 = 0 gives un-extrapolated A-HALS (Sec. 2) */
+    double eta;              /* shrink factor on restart (1.5)                */
+    double gamma;            /* growth factor of beta (1.01)                  */
+    double gamma_bar;        /* growth factor of beta_bar (1.005);
+                                1 < gamma_bar < gamma < eta is required        */
+    int32_t lw, lh;          /* inner HALS sweeps on W / on H; 0 = the A-HALS
+                                budget floor(1 + alpha*rho) of Gillis & Glineur
+                                (2012), computed by nmf_sweep_counts            */
+    double alpha;            /* alpha of that budget (0.5)                    */
+    int32_t project_w;       /* 1: W_y = max(0, W_y) after extrapolation (the
+                                paper's Algorithm 2 does not project W_y; 0)  */
+    int32_t compare_prev;    /* 0: restart when e(k) exceeds the error of the
+                                last accepted iterate (default); 1: when it
+                                exceeds e(k-1) as computed                      */
+    int32_t precision;       /* nmf_precision (NMF_PREC_FP32)                 */
+    int64_t trace_capacity;  /* initial device trace length (0 = 4096); grows */
+} nmf_params;
+
+typedef struct {
+    int64_t k;               /* outer iterations done                         */
+    double e_last;           /* error of the last accepted iterate            */
+    double e_k;              /* e(k) of the last iteration (accepted or not)  */
+    double fro2;             /* ||X||_F^2                                     */
+    double relerr;           /* e_last / ||X||_F                              */
+    double beta, beta_bar, beta_prev;  /* Algorithm 3 state for iteration k+1 */
+    int32_t accepted;        /* decision of the last iteration                */
+    int32_t lw, lh;          /* sweep budgets in use                          */
+    int32_t device_status;   /* sticky device-side status (nmf_status)        */
+    int32_t launches_per_iter; /* kernels one outer iteration launches        */
+} nmf_info;
+
+typedef struct {
+    int64_t iters;           /* iterations run by this call                   */
+    double relerr;           /* e_last / ||X||_F at return                    */
+    double seconds;          /* wall time of the call                         */
+    int32_t reached;         /* 1 when relerr <= target was observed          */
+} nmf_result;
+
+typedef struct nmf_handle nmf_handle;
+
+/* Fills *p with the defaults above (the paper's final E-A-HALS settings,
+ * Sec. 4.3.2: hp = 3, beta0 = 0.5, eta = 1.5, gamma = 1.01,
+ * gamma_bar = 1.005). */
+nmf_status nmf_params_default(nmf_params *p);
+
+/* A-HALS inner-sweep budget (Gillis & Glineur 2012, cited in Sec. 1):
+ * rho_W = 1 + (K + n r)/(m (r+1)), L_W = floor(1 + alpha rho_W);
+ * rho_H = 1 + (K + m r)/(n (r+1)), L_H = floor(1 + alpha rho_H);
+ * K = stored entries of X (m n if dense).  Pure host arithmetic. */
+nmf_status nmf_sweep_counts(int64_t m, int64_t n, int64_t K, int32_t r,
+                            double alpha, int32_t *lw, int32_t *lh);
+
+/* Creates a solver: validates the inputs, copies X, W0 (m x r) and H0
+ * (r x n) to the device (factors_on_device selects how W0/H0 are read),
+ * computes ||X||_F^2 and e(0) = ||X - W0 H0||_F (Algorithm 2, step 1) and
+ * sets W_y = W0, H_y = H0, beta = beta0, beta_bar = 1.
+ * Errors: NMF_EINVAL for m, n, r < 1, a malformed CSR, hp outside {1,2,3},
+ * parameters outside 0 <= beta0 <= 1 and 1 < gamma_bar < gamma < eta,
+ * negative or non-finite W0/H0; NMF_ENONFINITE for NaN/Inf in X;
+ * NMF_ENOTSUP for r > 128; NMF_ENOMEM / NMF_ECUDA from the device.
+ * On failure *out is set to NULL and nothing is leaked. */
+nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r,
+                      const float *W0, const float *H0,
+                      int32_t factors_on_device, const nmf_params *p,
+                      void *stream);
+
+/* Enqueues `iters` outer iterations of Algorithm 2 (steps 3-20) with the
+ * beta update of Algorithm 3 on the handle's stream; no host
+ * synchronisation and no device-to-host traffic.  The restart decisions and
+ * the beta schedule run on the device. */
+nmf_status nmf_step(nmf_handle *h, int32_t iters);
+
+/* Runs up to max_iters iterations in chunks of `check_every` (>= 1),
+ * reading e_last back after each chunk, and stops early once
+ * e_last / ||X||_F <= target_relerr (target <= 0 disables the test).
+ * Synchronises the stream; fills *res when res != NULL. */
+nmf_status nmf_solve(nmf_handle *h, int64_t max_iters, double target_relerr,
+                     int32_t check_every, nmf_result *res);
+
+/* Synchronises the stream and reports the scalar state. */
+nmf_status nmf_get_info(nmf_handle *h, nmf_info *info);
+
+/* Copies the accepted iterate (W, H) -- the pair Algorithm 2 returns --
+ * into W (m x r) and H (r x n), host or device per to_device.  Either
+ * pointer may be NULL to skip it.  Synchronises the stream. */
+nmf_status nmf_get_factors(nmf_handle *h, float *W, float *H,
+                           int32_t to_device);
+
+/* Copies the extrapolated pair (W_y, H_y) that the next iteration starts
+ * from.  Same conventions as nmf_get_factors. */
+nmf_status nmf_get_extrapolated(nmf_handle *h, float *Wy, float *Hy,
+                                int32_t to_device);
+
+/* Copies the per-iteration trace to host arrays of length `cap`: e(k), the
+ * beta_k used by iteration k, and the accept (1) / restart (0) decision.
+ * Any of the three pointers may be NULL.  *len receives min(k, cap). */
+nmf_status nmf_get_trace(nmf_handle *h, double *e, double *beta,
+                         uint8_t *accepted, int64_t cap, int64_t *len);
+
+/* Full solver state for checkpoint/resume and for replaying a step from an
+ * identical state.  The four factor arrays are host or device per
+ * on_device; sizes as above. */
+typedef struct {
+    double beta, beta_bar, beta_prev;  /* Algorithm 3 */
+    double e_last;           /* error the next e(k) is compared with          */
+    double e_prev;           /* e(k-1) as computed                            */
+    int64_t k;               /* iterations done                               */
+} nmf_scalars;
+
+nmf_status nmf_get_state(nmf_handle *h, nmf_scalars *s, float *W, float *H,
+                         float *Wy, float *Hy, int32_t to_device);
+nmf_status nmf_set_state(nmf_handle *h, const nmf_scalars *s, const float *W,
+                         const float *H, const float *Wy, const float *Hy,
+                         int32_t on_device);
+
+/* Phases of one outer iteration, in launch order (nmf_profile_phases). */
+typedef enum {
+    NMF_PHASE_GRAM_W = 0,    /* G = W_y^T W_y                                 */
+    NMF_PHASE_WTX = 1,       /* A = W_y^T X            (streams X)            */
+    NMF_PHASE_HALS_H = 2,    /* H sweeps + extrapolate/project H (steps 3-9)  */
+    NMF_PHASE_GRAM_H = 3,    /* D = H_y H_y^T                                 */
+    NMF_PHASE_XHT = 4,       /* C = X H_y^T            (streams X)            */
+    NMF_PHASE_HALS_W = 5,    /* W sweeps + e(k), restart decision, Alg. 3     */
+    NMF_PHASE_FINALIZE = 6,  /* extrapolate W (and H for hp = 1), accept/restart */
+    NMF_NUM_PHASES = 7
+} nmf_phase;
+
+/* Runs `iters` (>= 1) real outer iterations WITHOUT the CUDA graph, with a
+ * CUDA event recorded on the handle's stream between consecutive phases,
+ * and writes the mean device time of each phase in milliseconds to
+ * ms[NMF_NUM_PHASES].  The iterations advance the solver exactly like
+ * nmf_step.  Synchronises the stream. */
+nmf_status nmf_profile_phases(nmf_handle *h, int32_t iters, double *ms);
+
+/* Releases every device and host resource of the handle (NULL is a no-op).
+ * Synchronises the stream first. */
+nmf_status nmf_destroy(nmf_handle *h);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *nmf_last_error(void);
+
+/* Library version string. */
+const char *nmf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,748 @@
+// capi.cu -- the extern "C" boundary of libnmf_gb300 (declared in
+// include/nmf.h and include/nmf_ops.h).
+//
+// One outer iteration of Algorithm 2 (Ang & Gillis, arXiv 1805.06604) is
+// the launch sequence
+//   G = W_y^T W_y;  A = W_y^T X                        (inputs of step 3)
+//   H_n = HALS sweeps from H_y; H_y' = H_n + beta (H_n - H) [hp >= 2]
+//                                                       (steps 3-9, fused)
+//   D = H_y' H_y'^T;  C = X H_y'^T                      (inputs of step 10)
+//   W_n = HALS sweeps from W_y; e(k) by Remark 1; restart decision and
+//   Algorithm 3 in the last CTA                         (steps 10, 15-20)
+//   finalize: W_y = W_n + beta (W_n - W), H_y for hp = 1, accept/restart
+//                                                       (steps 11-14, 17, 19)
+// captured once into a CUDA graph and replayed by nmf_step.  Nothing in the
+// loop reads back to the host.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "nmf.h"
+
+using namespace nmfg;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+nmf_status fail(nmf_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+nmf_status fail(nmf_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define NMF_CUDA(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? NMF_ENOMEM : NMF_ECUDA,          \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                         \
+    } while (0)
+
+inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct nmf_handle {
+    cudaStream_t st = nullptr;          // caller's stream
+    cudaStream_t cap = nullptr;         // private stream used for graph capture
+    int64_t m = 0, n = 0, ld = 0, nnz = 0;
+    int r = 0, rs = 0;
+    int is_csr = 0;
+    nmf_params p{};
+    int lw = 0, lh = 0;
+    // X
+    float *X = nullptr;                          // dense m x ld
+    int64_t *rowptr = nullptr;                   // CSR of X
+    int32_t *colidx = nullptr;
+    float *val = nullptr;
+    int64_t *colptr = nullptr;                   // CSC of X (CSR of X^T)
+    int32_t *rowidx = nullptr;
+    float *cval = nullptr;
+    float *Ht = nullptr;                         // n x rs transpose of H_y' (CSR path)
+    // factors and products
+    float *W = nullptr, *H = nullptr, *Wy = nullptr, *Hy = nullptr;
+    float *Wn = nullptr, *Hn = nullptr, *Hw = nullptr;
+    float *A = nullptr, *C = nullptr, *G = nullptr, *D = nullptr;
+    double *fro2 = nullptr;
+    DevState *state = nullptr;
+    ErrPartial *partials = nullptr;
+    unsigned int *counter = nullptr;
+    unsigned int *tickets = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int *flag = nullptr;
+    // trace
+    double *tr_e = nullptr, *tr_beta = nullptr;
+    unsigned char *tr_acc = nullptr;
+    int64_t tr_cap = 0;
+    int64_t k_enq = 0;                           // iterations enqueued so far
+    // graph of one iteration
+    cudaGraphExec_t exec = nullptr;
+    DevState *h_state = nullptr;                 // pinned mirror for readback
+};
+
+namespace {
+
+void free_handle(nmf_handle *h) {
+    if (!h) return;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    void *ptrs[] = {h->X, h->rowptr, h->colidx, h->val, h->colptr, h->rowidx, h->cval, h->Ht,
+                    h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn, h->Hw, h->A, h->C, h->G, h->D,
+                    h->fro2, h->state, h->partials, h->counter, h->tickets, h->ws, h->flag,
+                    h->tr_e, h->tr_beta, h->tr_acc};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (h->h_state) cudaFreeHost(h->h_state);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    return e;
+}
+
+DevParams dev_params(const nmf_handle *h) {
+    DevParams d;
+    d.hp = h->p.hp;
+    d.project_w = h->p.project_w;
+    d.compare_prev = h->p.compare_prev;
+    d.eta = h->p.eta;
+    d.gamma = h->p.gamma;
+    d.gamma_bar = h->p.gamma_bar;
+    return d;
+}
+
+// X products for the current layout.
+cudaError_t enqueue_wtx(nmf_handle *h, const float *Wsrc, cudaStream_t st) {
+    if (h->is_csr)
+        return launch_wtx_csc(h->colptr, h->rowidx, h->cval, h->n, h->r, h->rs, Wsrc, h->A, h->ld,
+                              st);
+    return launch_wtx_f32(h->X, h->m, h->ld, h->ld, h->r, Wsrc, h->rs, h->A, h->ws, h->tickets,
+                          st);
+}
+
+cudaError_t enqueue_xht(nmf_handle *h, const float *Hsrc, cudaStream_t st) {
+    if (h->is_csr) {
+        cudaError_t e = launch_transpose_h(Hsrc, h->r, h->n, h->ld, h->Ht, h->rs, st);
+        if (e != cudaSuccess) return e;
+        return launch_xht_csr(h->rowptr, h->colidx, h->val, h->m, h->r, h->rs, h->Ht, h->C, st);
+    }
+    return launch_xht_f32(h->X, h->m, h->ld, h->r, Hsrc, h->ld, h->C, h->rs, st);
+}
+
+// One outer iteration of Algorithm 2, enqueued on st.  When ev != nullptr,
+// ev[i] is recorded before phase i and ev[NMF_NUM_PHASES] after the last.
+cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = nullptr) {
+    cudaError_t e;
+    auto mark = [&](int i) -> cudaError_t {
+        return ev ? cudaEventRecord(ev[i], st) : cudaSuccess;
+    };
+#define NMF_STEP(expr)                \
+    do {                              \
+        e = (expr);                   \
+        if (e != cudaSuccess) return e; \
+    } while (0)
+    NMF_STEP(mark(NMF_PHASE_GRAM_W));
+    NMF_STEP(launch_gram_rows(h->Wy, h->m, h->rs, h->r, h->rs, h->G, h->ws, st));
+    NMF_STEP(mark(NMF_PHASE_WTX));
+    NMF_STEP(enqueue_wtx(h, h->Wy, st));
+    NMF_STEP(mark(NMF_PHASE_HALS_H));
+    HEpilogue hep{};
+    hep.H_acc = h->H;
+    hep.Hw = h->p.hp >= 2 ? h->Hw : nullptr;
+    hep.state = h->state;
+    hep.hp = h->p.hp;
+    NMF_STEP(launch_hals_h(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hy, h->Hn, h->lh, hep, st));
+    const float *Hused = h->p.hp >= 2 ? h->Hw : h->Hn;
+    NMF_STEP(mark(NMF_PHASE_GRAM_H));
+    NMF_STEP(launch_gram_cols(Hused, h->n, h->ld, h->r, h->rs, h->D, h->ws, st));
+    NMF_STEP(mark(NMF_PHASE_XHT));
+    NMF_STEP(enqueue_xht(h, Hused, st));
+    NMF_STEP(mark(NMF_PHASE_HALS_W));
+    WEpilogue wep{};
+    wep.partials = h->partials;
+    wep.counter = h->counter;
+    wep.state = h->state;
+    wep.params = dev_params(h);
+    wep.trace.e = h->tr_e;
+    wep.trace.beta = h->tr_beta;
+    wep.trace.acc = h->tr_acc;
+    wep.trace.cap = h->tr_cap;
+    NMF_STEP(launch_hals_w(h->m, h->r, h->rs, h->C, h->D, h->Wy, h->Wn, h->lw, wep, st));
+    NMF_STEP(mark(NMF_PHASE_FINALIZE));
+    NMF_STEP(launch_finalize(h->m, h->rs, h->r, h->ld, h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn,
+                             h->Hw, h->state, dev_params(h), st));
+    NMF_STEP(mark(NMF_NUM_PHASES));
+#undef NMF_STEP
+    return cudaSuccess;
+}
+
+nmf_status build_graph(nmf_handle *h) {
+    if (h->exec) {
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    NMF_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_iteration(h, h->cap);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(NMF_ECUDA, "graph capture of one iteration failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&h->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(NMF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return NMF_OK;
+}
+
+nmf_status ensure_trace(nmf_handle *h, int64_t need) {
+    if (need <= h->tr_cap) return NMF_OK;
+    int64_t cap = std::max<int64_t>(need, 2 * h->tr_cap);
+    double *e = nullptr, *b = nullptr;
+    unsigned char *a = nullptr;
+    NMF_CUDA(cudaStreamSynchronize(h->st));
+    if (dalloc(&e, cap) != cudaSuccess || dalloc(&b, cap) != cudaSuccess ||
+        dalloc(&a, cap) != cudaSuccess) {
+        cudaFree(e);
+        cudaFree(b);
+        cudaFree(a);
+        return fail(NMF_ENOMEM, "trace allocation of %lld entries failed", (long long)cap);
+    }
+    if (h->tr_cap > 0) {
+        NMF_CUDA(cudaMemcpy(e, h->tr_e, sizeof(double) * h->tr_cap, cudaMemcpyDeviceToDevice));
+        NMF_CUDA(cudaMemcpy(b, h->tr_beta, sizeof(double) * h->tr_cap, cudaMemcpyDeviceToDevice));
+        NMF_CUDA(cudaMemcpy(a, h->tr_acc, h->tr_cap, cudaMemcpyDeviceToDevice));
+    }
+    cudaFree(h->tr_e);
+    cudaFree(h->tr_beta);
+    cudaFree(h->tr_acc);
+    h->tr_e = e;
+    h->tr_beta = b;
+    h->tr_acc = a;
+    h->tr_cap = cap;
+    return build_graph(h);
+}
+
+cudaMemcpyKind kind_of(int src_dev, int dst_dev) {
+    if (src_dev && dst_dev) return cudaMemcpyDeviceToDevice;
+    if (src_dev) return cudaMemcpyDeviceToHost;
+    if (dst_dev) return cudaMemcpyHostToDevice;
+    return cudaMemcpyHostToHost;
+}
+
+nmf_status check_params(const nmf_params *p) {
+    if (p->hp < 1 || p->hp > 3) return fail(NMF_EINVAL, "hp must be 1, 2 or 3 (got %d)", p->hp);
+    if (!(p->beta0 >= 0.0 && p->beta0 <= 1.0))
+        return fail(NMF_EINVAL, "beta0 must lie in [0, 1] (got %g)", p->beta0);
+    if (!(1.0 < p->gamma_bar && p->gamma_bar < p->gamma && p->gamma < p->eta))
+        return fail(NMF_EINVAL, "Algorithm 3 needs 1 < gamma_bar < gamma < eta (got %g, %g, %g)",
+                    p->gamma_bar, p->gamma, p->eta);
+    if (p->lw < 0 || p->lh < 0) return fail(NMF_EINVAL, "sweep counts must be >= 0");
+    if (p->lw == 0 || p->lh == 0)
+        if (!(p->alpha > 0.0)) return fail(NMF_EINVAL, "alpha must be > 0");
+    if (p->precision < NMF_PREC_FP32 || p->precision > NMF_PREC_BF16X3)
+        return fail(NMF_EINVAL, "unknown precision %d", p->precision);
+    if (p->precision != NMF_PREC_FP32)
+        return fail(NMF_ENOTSUP, "precision %d is not available in this build", p->precision);
+    return NMF_OK;
+}
+
+// Host-side CSR validation and transpose (creation-time layout preparation).
+nmf_status prepare_csr(const nmf_matrix *X, std::vector<int64_t> &rp, std::vector<int32_t> &ci,
+                       std::vector<float> &v, std::vector<int64_t> &cp, std::vector<int32_t> &ri,
+                       std::vector<float> &cv) {
+    const int64_t m = X->m, n = X->n, nnz = X->nnz;
+    rp.resize(m + 1);
+    ci.resize(nnz);
+    v.resize(nnz);
+    cudaMemcpyKind k = X->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    NMF_CUDA(cudaMemcpy(rp.data(), X->rowptr, sizeof(int64_t) * (m + 1), k));
+    if (nnz > 0) {
+        NMF_CUDA(cudaMemcpy(ci.data(), X->colidx, sizeof(int32_t) * nnz, k));
+        NMF_CUDA(cudaMemcpy(v.data(), X->values, sizeof(float) * nnz, k));
+    }
+    if (rp[0] != 0 || rp[m] != nnz) return fail(NMF_EINVAL, "CSR rowptr must run from 0 to nnz");
+    for (int64_t i = 0; i < m; ++i)
+        if (rp[i + 1] < rp[i]) return fail(NMF_EINVAL, "CSR rowptr decreases at row %lld", (long long)i);
+    for (int64_t q = 0; q < nnz; ++q) {
+        if (ci[q] < 0 || ci[q] >= n)
+            return fail(NMF_EINVAL, "CSR column index %d out of [0, %lld)", ci[q], (long long)n);
+        if (!std::isfinite(v[q])) return fail(NMF_ENONFINITE, "X holds a NaN or Inf");
+    }
+    // CSC by a stable counting sort on the column (rows stay ascending).
+    cp.assign(n + 1, 0);
+    for (int64_t q = 0; q < nnz; ++q) cp[ci[q] + 1]++;
+    for (int64_t j = 0; j < n; ++j) cp[j + 1] += cp[j];
+    ri.resize(nnz);
+    cv.resize(nnz);
+    std::vector<int64_t> pos(cp.begin(), cp.end() - 1);
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+            const int64_t d = pos[ci[q]]++;
+            ri[d] = (int32_t)i;
+            cv[d] = v[q];
+        }
+    return NMF_OK;
+}
+
+nmf_status check_factor_host(const float *p, int64_t count, const char *name) {
+    for (int64_t q = 0; q < count; ++q)
+        if (!(p[q] >= 0.0f) || !std::isfinite(p[q]))
+            return fail(NMF_EINVAL, "%s must be finite and nonnegative (entry %lld is %g)", name,
+                        (long long)q, (double)p[q]);
+    return NMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *nmf_last_error(void) { return g_err; }
+
+const char *nmf_version(void) { return "nmf_gb300 0.1 (sm_103a)"; }
+
+nmf_status nmf_params_default(nmf_params *p) {
+    if (!p) return fail(NMF_EINVAL, "params pointer is NULL");
+    memset(p, 0, sizeof(*p));
+    p->hp = 3;
+    p->beta0 = 0.5;
+    p->eta = 1.5;
+    p->gamma = 1.01;
+    p->gamma_bar = 1.005;
+    p->lw = 0;
+    p->lh = 0;
+    p->alpha = 0.5;
+    p->project_w = 0;
+    p->compare_prev = 0;
+    p->precision = NMF_PREC_FP32;
+    p->trace_capacity = 4096;
+    return NMF_OK;
+}
+
+nmf_status nmf_sweep_counts(int64_t m, int64_t n, int64_t K, int32_t r, double alpha,
+                            int32_t *lw, int32_t *lh) {
+    if (m < 1 || n < 1 || r < 1 || K < 0 || !(alpha > 0.0) || !lw || !lh)
+        return fail(NMF_EINVAL, "nmf_sweep_counts: bad arguments");
+    const double rho_w = 1.0 + ((double)K + (double)n * r) / ((double)m * (r + 1));
+    const double rho_h = 1.0 + ((double)K + (double)m * r) / ((double)n * (r + 1));
+    *lw = (int32_t)floor(1.0 + alpha * rho_w);
+    *lh = (int32_t)floor(1.0 + alpha * rho_h);
+    return NMF_OK;
+}
+
+nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const float *W0,
+                      const float *H0, int32_t factors_on_device, const nmf_params *pin,
+                      void *stream) {
+    if (!out) return fail(NMF_EINVAL, "out pointer is NULL");
+    *out = nullptr;
+    if (!X || !W0 || !H0) return fail(NMF_EINVAL, "X, W0 and H0 are required");
+    if (X->m < 1 || X->n < 1 || r < 1) return fail(NMF_EINVAL, "m, n and r must be >= 1");
+    if (r > kMaxRank) return fail(NMF_ENOTSUP, "r = %d exceeds the build cap %d", r, kMaxRank);
+    if (X->format != NMF_DENSE && X->format != NMF_CSR)
+        return fail(NMF_EINVAL, "unknown matrix format %d", X->format);
+    if (!X->values) return fail(NMF_EINVAL, "X values pointer is NULL");
+    if (X->format == NMF_CSR && (!X->rowptr || (X->nnz > 0 && !X->colidx) || X->nnz < 0))
+        return fail(NMF_EINVAL, "CSR X needs rowptr, colidx and nnz >= 0");
+    if (X->format == NMF_DENSE && X->ld != 0 && X->ld < X->n)
+        return fail(NMF_EINVAL, "dense ld must be >= n");
+    nmf_params p;
+    if (pin) p = *pin;
+    else nmf_params_default(&p);
+    nmf_status s = check_params(&p);
+    if (s != NMF_OK) return s;
+
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+        cudaGetLastError();
+        return fail(NMF_ECUDA, "no CUDA device is available (this library has no CPU path)");
+    }
+
+    nmf_handle *h = new (std::nothrow) nmf_handle();
+    if (!h) return fail(NMF_ENOMEM, "host allocation failed");
+    h->st = static_cast<cudaStream_t>(stream);
+    h->m = X->m;
+    h->n = X->n;
+    h->r = r;
+    h->rs = (int)round_up(r, 8);
+    h->ld = round_up(X->n, 8);
+    h->is_csr = X->format == NMF_CSR;
+    h->nnz = h->is_csr ? X->nnz : X->m * X->n;
+    h->p = p;
+    int32_t lw = p.lw, lh = p.lh;
+    if (lw == 0 || lh == 0) {
+        int32_t aw, ah;
+        nmf_sweep_counts(h->m, h->n, h->nnz, r, p.alpha, &aw, &ah);
+        if (lw == 0) lw = aw;
+        if (lh == 0) lh = ah;
+    }
+    h->lw = lw;
+    h->lh = lh;
+
+#define NMF_TRY(expr)                         \
+    do {                                      \
+        nmf_status s_ = (expr);               \
+        if (s_ != NMF_OK) {                   \
+            free_handle(h);                   \
+            return s_;                        \
+        }                                     \
+    } while (0)
+#define NMF_TRYC(call) NMF_TRY([&]() -> nmf_status { NMF_CUDA(call); return NMF_OK; }())
+
+    const int64_t m = h->m, n = h->n, ld = h->ld, rs = h->rs;
+    NMF_TRYC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    NMF_TRYC(dalloc(&h->W, m * rs));
+    NMF_TRYC(dalloc(&h->Wy, m * rs));
+    NMF_TRYC(dalloc(&h->Wn, m * rs));
+    NMF_TRYC(dalloc(&h->C, m * rs));
+    NMF_TRYC(dalloc(&h->H, r * ld));
+    NMF_TRYC(dalloc(&h->Hy, r * ld));
+    NMF_TRYC(dalloc(&h->Hn, r * ld));
+    NMF_TRYC(dalloc(&h->Hw, r * ld));
+    NMF_TRYC(dalloc(&h->A, r * ld));
+    NMF_TRYC(dalloc(&h->G, rs * rs));
+    NMF_TRYC(dalloc(&h->D, rs * rs));
+    NMF_TRYC(dalloc(&h->fro2, 1));
+    NMF_TRYC(dalloc(&h->state, 1));
+    NMF_TRYC(dalloc(&h->flag, 1));
+    const int npart = std::max(hals_w_num_ctas(m, r), err_rows_num_ctas(m));
+    NMF_TRYC(dalloc(&h->partials, npart));
+    NMF_TRYC(dalloc(&h->counter, 1));
+    NMF_TRYC(dalloc(&h->tickets, wtx_num_tickets(ld)));
+    NMF_TRYC(cudaHostAlloc((void **)&h->h_state, sizeof(DevState), cudaHostAllocDefault));
+    size_t ws = std::max(gram_ws_bytes(m, (int)rs), gram_ws_bytes(n, (int)rs));
+    ws = std::max(ws, fro2_ws_bytes(m * ld));
+    if (!h->is_csr) ws = std::max(ws, wtx_ws_bytes(m, ld, r));
+    h->ws_bytes = ws;
+    NMF_TRYC(cudaMalloc(&h->ws, ws));
+
+    cudaStream_t st = h->st;
+    for (void *q : {(void *)h->W, (void *)h->Wy, (void *)h->Wn, (void *)h->C})
+        NMF_TRYC(cudaMemsetAsync(q, 0, sizeof(float) * m * rs, st));
+    for (void *q : {(void *)h->H, (void *)h->Hy, (void *)h->Hn, (void *)h->Hw, (void *)h->A})
+        NMF_TRYC(cudaMemsetAsync(q, 0, sizeof(float) * r * ld, st));
+    NMF_TRYC(cudaMemsetAsync(h->G, 0, sizeof(float) * rs * rs, st));
+    NMF_TRYC(cudaMemsetAsync(h->D, 0, sizeof(float) * rs * rs, st));
+    NMF_TRYC(cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), st));
+    NMF_TRYC(cudaMemsetAsync(h->tickets, 0, sizeof(unsigned int) * wtx_num_tickets(ld), st));
+    NMF_TRYC(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
+    NMF_TRYC(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
+
+    // Factors: validate on the host (copying device inputs down), then pack.
+    {
+        std::vector<float> w(m * r), hh(r * n);
+        cudaMemcpyKind kd = factors_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        NMF_TRYC(cudaMemcpy(w.data(), W0, sizeof(float) * m * r, kd));
+        NMF_TRYC(cudaMemcpy(hh.data(), H0, sizeof(float) * r * n, kd));
+        NMF_TRY(check_factor_host(w.data(), m * r, "W0"));
+        NMF_TRY(check_factor_host(hh.data(), r * n, "H0"));
+        NMF_TRYC(cudaMemcpy2DAsync(h->W, sizeof(float) * rs, w.data(), sizeof(float) * r,
+                                   sizeof(float) * r, m, cudaMemcpyHostToDevice, st));
+        NMF_TRYC(cudaMemcpy2DAsync(h->H, sizeof(float) * ld, hh.data(), sizeof(float) * n,
+                                   sizeof(float) * n, r, cudaMemcpyHostToDevice, st));
+        NMF_TRYC(cudaStreamSynchronize(st));
+    }
+    NMF_TRYC(cudaMemcpyAsync(h->Wy, h->W, sizeof(float) * m * rs, cudaMemcpyDeviceToDevice, st));
+    NMF_TRYC(cudaMemcpyAsync(h->Hy, h->H, sizeof(float) * r * ld, cudaMemcpyDeviceToDevice, st));
+
+    // X.
+    if (h->is_csr) {
+        std::vector<int64_t> rp, cp;
+        std::vector<int32_t> ci, ri;
+        std::vector<float> v, cv;
+        NMF_TRY(prepare_csr(X, rp, ci, v, cp, ri, cv));
+        const int64_t nnz = h->nnz;
+        NMF_TRYC(dalloc(&h->rowptr, m + 1));
+        NMF_TRYC(dalloc(&h->colidx, nnz));
+        NMF_TRYC(dalloc(&h->val, nnz));
+        NMF_TRYC(dalloc(&h->colptr, n + 1));
+        NMF_TRYC(dalloc(&h->rowidx, nnz));
+        NMF_TRYC(dalloc(&h->cval, nnz));
+        NMF_TRYC(dalloc(&h->Ht, n * rs));
+        NMF_TRYC(cudaMemsetAsync(h->Ht, 0, sizeof(float) * n * rs, st));
+        NMF_TRYC(cudaMemcpyAsync(h->rowptr, rp.data(), sizeof(int64_t) * (m + 1),
+                                 cudaMemcpyHostToDevice, st));
+        NMF_TRYC(cudaMemcpyAsync(h->colptr, cp.data(), sizeof(int64_t) * (n + 1),
+                                 cudaMemcpyHostToDevice, st));
+        if (nnz > 0) {
+            NMF_TRYC(cudaMemcpyAsync(h->colidx, ci.data(), sizeof(int32_t) * nnz,
+                                     cudaMemcpyHostToDevice, st));
+            NMF_TRYC(cudaMemcpyAsync(h->val, v.data(), sizeof(float) * nnz,
+                                     cudaMemcpyHostToDevice, st));
+            NMF_TRYC(cudaMemcpyAsync(h->rowidx, ri.data(), sizeof(int32_t) * nnz,
+                                     cudaMemcpyHostToDevice, st));
+            NMF_TRYC(cudaMemcpyAsync(h->cval, cv.data(), sizeof(float) * nnz,
+                                     cudaMemcpyHostToDevice, st));
+        }
+        NMF_TRYC(cudaStreamSynchronize(st));
+        NMF_TRYC(launch_fro2(h->val, 1, nnz, nnz, h->fro2, h->ws, st));
+    } else {
+        const int64_t xld = X->ld ? X->ld : n;
+        NMF_TRYC(dalloc(&h->X, m * ld));
+        NMF_TRYC(cudaMemsetAsync(h->X, 0, sizeof(float) * m * ld, st));
+        NMF_TRYC(cudaMemcpy2DAsync(h->X, sizeof(float) * ld, X->values, sizeof(float) * xld,
+                                   sizeof(float) * n, m,
+                                   X->on_device ? cudaMemcpyDeviceToDevice
+                                                : cudaMemcpyHostToDevice,
+                                   st));
+        NMF_TRYC(launch_nonfinite_scan(h->X, m * ld, h->flag, st));
+        int bad = 0;
+        NMF_TRYC(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        NMF_TRYC(cudaStreamSynchronize(st));
+        if (bad) {
+            free_handle(h);
+            return fail(NMF_ENONFINITE, "X holds a NaN or Inf");
+        }
+        NMF_TRYC(launch_fro2(h->X, m, ld, ld, h->fro2, h->ws, st));
+    }
+
+    // e(0) = ||X - W H||_F via Remark 1 (Algorithm 2 step 1).
+    NMF_TRYC(launch_gram_cols(h->H, n, ld, r, (int)rs, h->D, h->ws, st));
+    NMF_TRYC(enqueue_xht(h, h->H, st));
+    NMF_TRYC(launch_init_state(m, r, (int)rs, h->W, h->C, h->D, h->fro2, h->state, p.beta0,
+                               h->partials, st));
+    NMF_TRYC(cudaStreamSynchronize(st));
+
+    int64_t cap = p.trace_capacity > 0 ? p.trace_capacity : 4096;
+    NMF_TRY(ensure_trace(h, cap));
+    NMF_TRYC(cudaStreamSynchronize(st));
+#undef NMF_TRYC
+#undef NMF_TRY
+    *out = h;
+    g_err[0] = 0;
+    return NMF_OK;
+}
+
+nmf_status nmf_step(nmf_handle *h, int32_t iters) {
+    if (!h) return fail(NMF_EINVAL, "handle is NULL");
+    if (iters < 0) return fail(NMF_EINVAL, "iters must be >= 0");
+    nmf_status s = ensure_trace(h, h->k_enq + iters);
+    if (s != NMF_OK) return s;
+    for (int32_t i = 0; i < iters; ++i) NMF_CUDA(cudaGraphLaunch(h->exec, h->st));
+    h->k_enq += iters;
+    return NMF_OK;
+}
+
+nmf_status nmf_get_info(nmf_handle *h, nmf_info *info) {
+    if (!h || !info) return fail(NMF_EINVAL, "handle and info are required");
+    NMF_CUDA(cudaMemcpyAsync(h->h_state, h->state, sizeof(DevState), cudaMemcpyDeviceToHost, h->st));
+    NMF_CUDA(cudaStreamSynchronize(h->st));
+    const DevState &d = *h->h_state;
+    info->k = d.k;
+    info->e_last = d.e_last;
+    info->e_k = d.e_k;
+    info->fro2 = d.fro2;
+    info->relerr = d.fro2 > 0.0 ? d.e_last / sqrt(d.fro2) : 0.0;
+    info->beta = d.beta;
+    info->beta_bar = d.beta_bar;
+    info->beta_prev = d.beta_prev;
+    info->accepted = d.accepted;
+    info->lw = h->lw;
+    info->lh = h->lh;
+    info->device_status = d.status;
+    // gram W (2) + W^T X (1, or 1 for CSC) + H sweeps (1) + gram H (2) +
+    // X H^T (1; CSR adds the H transpose) + W sweeps (1) + finalize (1)
+    info->launches_per_iter = h->is_csr ? 10 : 9;
+    return NMF_OK;
+}
+
+nmf_status nmf_solve(nmf_handle *h, int64_t max_iters, double target_relerr, int32_t check_every,
+                     nmf_result *res) {
+    if (!h) return fail(NMF_EINVAL, "handle is NULL");
+    if (max_iters < 0 || check_every < 1) return fail(NMF_EINVAL, "bad max_iters / check_every");
+    auto t0 = std::chrono::steady_clock::now();
+    int64_t done = 0;
+    int reached = 0;
+    nmf_info info{};
+    while (done < max_iters) {
+        const int32_t chunk = (int32_t)std::min<int64_t>(check_every, max_iters - done);
+        nmf_status s = nmf_step(h, chunk);
+        if (s != NMF_OK) return s;
+        done += chunk;
+        s = nmf_get_info(h, &info);
+        if (s != NMF_OK) return s;
+        if (info.device_status != 0)
+            return fail((nmf_status)info.device_status, "device reported status %d after %lld iterations",
+                        info.device_status, (long long)info.k);
+        if (target_relerr > 0.0 && info.relerr <= target_relerr) {
+            reached = 1;
+            break;
+        }
+    }
+    if (done == 0) {
+        nmf_status s = nmf_get_info(h, &info);
+        if (s != NMF_OK) return s;
+    }
+    if (res) {
+        res->iters = done;
+        res->relerr = info.relerr;
+        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        res->reached = reached;
+    }
+    return NMF_OK;
+}
+
+static nmf_status copy_w_out(nmf_handle *h, const float *src, float *dst, int to_device) {
+    NMF_CUDA(cudaMemcpy2DAsync(dst, sizeof(float) * h->r, src, sizeof(float) * h->rs,
+                               sizeof(float) * h->r, h->m, kind_of(1, to_device), h->st));
+    return NMF_OK;
+}
+static nmf_status copy_h_out(nmf_handle *h, const float *src, float *dst, int to_device) {
+    NMF_CUDA(cudaMemcpy2DAsync(dst, sizeof(float) * h->n, src, sizeof(float) * h->ld,
+                               sizeof(float) * h->n, h->r, kind_of(1, to_device), h->st));
+    return NMF_OK;
+}
+static nmf_status copy_w_in(nmf_handle *h, const float *src, float *dst, int on_device) {
+    NMF_CUDA(cudaMemcpy2DAsync(dst, sizeof(float) * h->rs, src, sizeof(float) * h->r,
+                               sizeof(float) * h->r, h->m, kind_of(on_device, 1), h->st));
+    return NMF_OK;
+}
+static nmf_status copy_h_in(nmf_handle *h, const float *src, float *dst, int on_device) {
+    NMF_CUDA(cudaMemcpy2DAsync(dst, sizeof(float) * h->ld, src, sizeof(float) * h->n,
+                               sizeof(float) * h->n, h->r, kind_of(on_device, 1), h->st));
+    return NMF_OK;
+}
+
+nmf_status nmf_get_factors(nmf_handle *h, float *W, float *H, int32_t to_device) {
+    if (!h) return fail(NMF_EINVAL, "handle is NULL");
+    nmf_status s;
+    if (W && (s = copy_w_out(h, h->W, W, to_device)) != NMF_OK) return s;
+    if (H && (s = copy_h_out(h, h->H, H, to_device)) != NMF_OK) return s;
+    NMF_CUDA(cudaStreamSynchronize(h->st));
+    return NMF_OK;
+}
+
+nmf_status nmf_get_extrapolated(nmf_handle *h, float *Wy, float *Hy, int32_t to_device) {
+    if (!h) return fail(NMF_EINVAL, "handle is NULL");
+    nmf_status s;
+    if (Wy && (s = copy_w_out(h, h->Wy, Wy, to_device)) != NMF_OK) return s;
+    if (Hy && (s = copy_h_out(h, h->Hy, Hy, to_device)) != NMF_OK) return s;
+    NMF_CUDA(cudaStreamSynchronize(h->st));
+    return NMF_OK;
+}
+
+nmf_status nmf_get_trace(nmf_handle *h, double *e, double *beta, uint8_t *accepted, int64_t cap,
+                         int64_t *len) {
+    if (!h || cap < 0) return fail(NMF_EINVAL, "bad arguments");
+    nmf_info info;
+    nmf_status s = nmf_get_info(h, &info);
+    if (s != NMF_OK) return s;
+    int64_t n = std::min<int64_t>(std::min<int64_t>(info.k, h->tr_cap), cap);
+    if (n > 0) {
+        if (e) NMF_CUDA(cudaMemcpy(e, h->tr_e, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        if (beta) NMF_CUDA(cudaMemcpy(beta, h->tr_beta, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        if (accepted) NMF_CUDA(cudaMemcpy(accepted, h->tr_acc, n, cudaMemcpyDeviceToHost));
+    }
+    if (len) *len = n;
+    return NMF_OK;
+}
+
+nmf_status nmf_get_state(nmf_handle *h, nmf_scalars *s, float *W, float *H, float *Wy, float *Hy,
+                         int32_t to_device) {
+    if (!h) return fail(NMF_EINVAL, "handle is NULL");
+    nmf_status st;
+    if (W && (st = copy_w_out(h, h->W, W, to_device)) != NMF_OK) return st;
+    if (H && (st = copy_h_out(h, h->H, H, to_device)) != NMF_OK) return st;
+    if (Wy && (st = copy_w_out(h, h->Wy, Wy, to_device)) != NMF_OK) return st;
+    if (Hy && (st = copy_h_out(h, h->Hy, Hy, to_device)) != NMF_OK) return st;
+    NMF_CUDA(cudaMemcpyAsync(h->h_state, h->state, sizeof(DevState), cudaMemcpyDeviceToHost, h->st));
+    NMF_CUDA(cudaStreamSynchronize(h->st));
+    if (s) {
+        s->beta = h->h_state->beta;
+        s->beta_bar = h->h_state->beta_bar;
+        s->beta_prev = h->h_state->beta_prev;
+        s->e_last = h->h_state->e_last;
+        s->e_prev = h->h_state->e_prev;
+        s->k = h->h_state->k;
+    }
+    return NMF_OK;
+}
+
+nmf_status nmf_set_state(nmf_handle *h, const nmf_scalars *s, const float *W, const float *H,
+                         const float *Wy, const float *Hy, int32_t on_device) {
+    if (!h || !s || !W || !H || !Wy || !Hy) return fail(NMF_EINVAL, "all arguments are required");
+    if (s->k < 0) return fail(NMF_EINVAL, "k must be >= 0");
+    nmf_status st;
+    if ((st = copy_w_in(h, W, h->W, on_device)) != NMF_OK) return st;
+    if ((st = copy_h_in(h, H, h->H, on_device)) != NMF_OK) return st;
+    if ((st = copy_w_in(h, Wy, h->Wy, on_device)) != NMF_OK) return st;
+    if ((st = copy_h_in(h, Hy, h->Hy, on_device)) != NMF_OK) return st;
+    NMF_CUDA(cudaMemcpyAsync(h->h_state, h->state, sizeof(DevState), cudaMemcpyDeviceToHost, h->st));
+    NMF_CUDA(cudaStreamSynchronize(h->st));
+    DevState d = *h->h_state;
+    d.beta = s->beta;
+    d.beta_bar = s->beta_bar;
+    d.beta_prev = s->beta_prev;
+    d.e_last = s->e_last;
+    d.e_prev = s->e_prev;
+    d.k = s->k;
+    d.status = 0;
+    *h->h_state = d;
+    NMF_CUDA(cudaMemcpyAsync(h->state, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, h->st));
+    NMF_CUDA(cudaStreamSynchronize(h->st));
+    h->k_enq = s->k;
+    return ensure_trace(h, h->k_enq + 1);
+}
+
+nmf_status nmf_profile_phases(nmf_handle *h, int32_t iters, double *ms) {
+    if (!h || !ms || iters < 1) return fail(NMF_EINVAL, "handle, ms and iters >= 1 are required");
+    nmf_status s = ensure_trace(h, h->k_enq + iters);
+    if (s != NMF_OK) return s;
+    cudaEvent_t ev[NMF_NUM_PHASES + 1] = {};
+    for (int i = 0; i <= NMF_NUM_PHASES; ++i) {
+        cudaError_t e = cudaEventCreate(&ev[i]);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+            return fail(NMF_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+        }
+    }
+    double acc[NMF_NUM_PHASES] = {};
+    nmf_status out = NMF_OK;
+    for (int32_t it = 0; it < iters && out == NMF_OK; ++it) {
+        cudaError_t e = enqueue_iteration(h, h->st, ev);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[NMF_NUM_PHASES]);
+        if (e != cudaSuccess) {
+            out = fail(NMF_ECUDA, "profiled iteration failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        h->k_enq += 1;
+        for (int i = 0; i < NMF_NUM_PHASES; ++i) {
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+            acc[i] += t;
+        }
+    }
+    for (int i = 0; i <= NMF_NUM_PHASES; ++i) cudaEventDestroy(ev[i]);
+    if (out != NMF_OK) return out;
+    for (int i = 0; i < NMF_NUM_PHASES; ++i) ms[i] = acc[i] / iters;
+    return NMF_OK;
+}
+
+nmf_status nmf_destroy(nmf_handle *h) {
+    if (!h) return NMF_OK;
+    cudaStreamSynchronize(h->st);
+    free_handle(h);
+    return NMF_OK;
+}
+
+}  // extern "C"

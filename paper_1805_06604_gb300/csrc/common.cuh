@@ -1,0 +1,146 @@
+// common.cuh -- internal definitions shared by the CUDA translation units of
+// libnmf_gb300 (never included by the oracle or by callers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nmf.h"
+
+namespace nmfg {
+
+constexpr int kMaxRank = 128;      // build cap on r (nmf_create: NMF_ENOTSUP above)
+constexpr int kNumSMs = 152;       // GB300: 2 dies x 76 SMs
+
+// Device-resident scalar state of Algorithms 2 and 3.  Written only by the
+// single thread that takes the restart decision; read by every kernel of the
+// next iteration.
+struct DevState {
+    double beta;          // beta_k for the iteration about to run
+    double beta_bar;      // Algorithm 3 upper bound
+    double beta_prev;     // beta_{k-1}
+    double e_last;        // error the next e(k) is compared with
+    double e_prev;        // e(k-1) as computed
+    double fro2;          // ||X||_F^2
+    double e_k;           // e(k) of the last iteration
+    double beta_used;     // beta_k of the last iteration (the extrapolation step)
+    long long k;          // iterations done
+    int accepted;         // decision of the last iteration
+    int status;           // sticky nmf_status raised on the device
+};
+
+// Parameters the device logic needs (copied by value into kernel args).
+struct DevParams {
+    int hp;
+    int project_w;
+    int compare_prev;
+    double eta, gamma, gamma_bar;
+};
+
+// Trace written by the decision thread.
+struct DevTrace {
+    double *e;
+    double *beta;
+    unsigned char *acc;
+    long long cap;
+};
+
+// Error reduction partials of one W-sweep launch (Remark 1):
+// cross = <W_n, C>, quad = <W_n^T W_n, D> accumulated per CTA in FP64.
+struct ErrPartial {
+    double cross;
+    double quad;
+};
+
+}  // namespace nmfg
+
+// ----------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files, used by capi.cu).
+// Every launcher returns the cudaError_t of its launches.
+//
+// Internal layouts (the library's own copies, zero padded):
+//   X : m x ld   row-major, ld = n rounded up to a multiple of 8
+//   W, W_y, W_n, C : m x rs row-major, rs = r rounded up to a multiple of 8
+//   H, H_y, H_n, H_w, A : r x ld row-major
+//   G, D : rs x rs
+// ----------------------------------------------------------------------------
+namespace nmfg {
+
+// ||X||_F^2 in FP64 over rows x cols entries with row stride ld.
+size_t fro2_ws_bytes(int64_t count);
+cudaError_t launch_fro2(const float *vals, int64_t rows, int64_t cols, int64_t ld,
+                        double *out, void *ws, cudaStream_t st);
+
+// G = M^T M for M (N x ldm, r used columns) -- the Gram of W -- or
+// G = M M^T for M (r x ldm, N used columns) -- the Gram of H.  G is rs x rs.
+size_t gram_ws_bytes(int64_t N, int rs);
+cudaError_t launch_gram_rows(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
+                             void *ws, cudaStream_t st);
+cudaError_t launch_gram_cols(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
+                             void *ws, cudaStream_t st);
+
+// Dense products, FP32 on CUDA cores.  A = W^T X (r x ld), C = X H^T (m x rs).
+// The split-K of A needs ws (partial tiles) and wtx_num_tickets() zeroed
+// counters, which the kernel leaves at zero.
+size_t wtx_ws_bytes(int64_t m, int64_t ld, int r);
+int64_t wtx_num_tickets(int64_t ld);
+cudaError_t launch_wtx_f32(const float *X, int64_t m, int64_t lda, int64_t ldx, int r,
+                           const float *W, int rs, float *A, void *ws, unsigned int *tickets,
+                           cudaStream_t st);
+cudaError_t launch_xht_f32(const float *X, int64_t m, int64_t ldx, int r, const float *H,
+                           int64_t ldh, float *C, int rs, cudaStream_t st);
+
+// HALS sweeps.  H side: columns of H independent given A and G.  W side:
+// rows of W independent given C and D.
+struct HEpilogue {            // optional fused work after the H sweeps
+    const float *H_acc;       // accepted H (for the extrapolation)
+    float *Hw;                // where to write the H_y used by the W-update, or null
+    const DevState *state;    // beta_k
+    int hp;
+};
+struct WEpilogue {            // optional fused work after the W sweeps
+    ErrPartial *partials;     // one per CTA, or null (no error terms)
+    unsigned int *counter;    // last-CTA ticket (zero between launches)
+    DevState *state;          // decision + Algorithm 3, or null
+    DevParams params;
+    DevTrace trace;
+};
+cudaError_t launch_hals_h(int64_t n, int64_t ldh, int r, int rs, const float *A,
+                          const float *G, const float *H_in, float *H_out, int sweeps,
+                          const HEpilogue &ep, cudaStream_t st);
+cudaError_t launch_hals_w(int64_t m, int r, int rs, const float *C, const float *D,
+                          const float *W_in, float *W_out, int sweeps, const WEpilogue &ep,
+                          cudaStream_t st);
+int hals_w_num_ctas(int64_t m, int r);
+
+// Algorithm 2 steps 11-20 after the decision: extrapolation, projection and
+// accept/restart copies, W side and H side.
+cudaError_t launch_finalize(int64_t m, int rs, int r, int64_t ldh, float *W, float *H,
+                            float *Wy, float *Hy, const float *Wn, const float *Hn,
+                            const float *Hw, const DevState *state, DevParams p,
+                            cudaStream_t st);
+
+// Remark 1 error terms of (W, C = X H^T, D = H H^T), one partial per CTA.
+int err_rows_num_ctas(int64_t m);
+cudaError_t launch_err_rows(int64_t m, int r, int rs, const float *W, const float *C,
+                            const float *D, ErrPartial *part, cudaStream_t st);
+
+// e(0) (Algorithm 2 step 1) and the initial Algorithm 3 values.
+cudaError_t launch_init_state(int64_t m, int r, int rs, const float *W, const float *C,
+                              const float *D, const double *fro2, DevState *state,
+                              double beta0, ErrPartial *partials, cudaStream_t st);
+
+// Sparse X (csr.cu): C = X H^T from CSR with Ht = H^T (n x rs); A = W^T X
+// from the CSC copy; H (r x ldh) -> Ht.
+cudaError_t launch_xht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
+                           int64_t m, int r, int rs, const float *Ht, float *C, cudaStream_t st);
+cudaError_t launch_wtx_csc(const int64_t *colptr, const int32_t *rowidx, const float *val,
+                           int64_t n, int r, int rs, const float *W, float *A, int64_t lda,
+                           cudaStream_t st);
+cudaError_t launch_transpose_h(const float *H, int r, int64_t n, int64_t ldh, float *Ht, int rs,
+                               cudaStream_t st);
+
+// Sets *flag to 1 when v[0..count) holds a NaN or an Inf.
+cudaError_t launch_nonfinite_scan(const float *v, int64_t count, int *flag, cudaStream_t st);
+
+}  // namespace nmfg

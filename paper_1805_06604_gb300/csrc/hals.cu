@@ -1,0 +1,78 @@
+// hals.cu -- dispatch of the A-HALS sweep kernel (hals_impl.cuh): picks the
+// lanes per item T and the smallest instantiated slot count S >= ceil(r/T).
+#include "common.cuh"
+
+namespace nmfg {
+
+template <int T, int S, int LAYOUT>
+cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const float *G, int rs,
+                        const float *Xin, float *Xout, int sweeps, const HEpilogue &hep,
+                        const WEpilogue &wep, cudaStream_t st);
+
+namespace {
+
+constexpr int kSlots4[] = {2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 20, 24, 28, 32};
+constexpr int kSlots2[] = {2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 20, 24, 28, 32};
+constexpr int kThreadsPerCta = 128;
+
+template <int N>
+int pick(const int (&list)[N], int need) {
+    for (int v : list)
+        if (v >= need) return v;
+    return -1;
+}
+
+// Two lanes per item once the items fill every scheduler of the GPU with at
+// least one warp (and r <= 64); four lanes otherwise.
+int pick_lanes(int64_t items, int r) {
+    return (r <= 64 && items * 2 >= 4LL * kNumSMs * 32) ? 2 : 4;
+}
+
+template <int LAYOUT>
+cudaError_t dispatch(int64_t items, int r, int64_t ld, const float *A, const float *G, int rs,
+                     const float *Xin, float *Xout, int sweeps, const HEpilogue &hep,
+                     const WEpilogue &wep, cudaStream_t st) {
+    const int T = pick_lanes(items, r);
+    const int need = (r + T - 1) / T < 2 ? 2 : (r + T - 1) / T;
+#define NMF_HALS_CASE(TV, SV)                                                                \
+    case SV:                                                                                 \
+        return hals_launch<TV, SV, LAYOUT>(items, r, ld, A, G, rs, Xin, Xout, sweeps, hep, wep, \
+                                           st);
+    if (T == 2) {
+        switch (pick(kSlots2, need)) {
+            NMF_HALS_CASE(2, 2) NMF_HALS_CASE(2, 3) NMF_HALS_CASE(2, 4) NMF_HALS_CASE(2, 5) NMF_HALS_CASE(2, 6) NMF_HALS_CASE(2, 7) NMF_HALS_CASE(2, 8) NMF_HALS_CASE(2, 9) NMF_HALS_CASE(2, 10) NMF_HALS_CASE(2, 11) NMF_HALS_CASE(2, 12) NMF_HALS_CASE(2, 13) NMF_HALS_CASE(2, 14) NMF_HALS_CASE(2, 15) NMF_HALS_CASE(2, 16) NMF_HALS_CASE(2, 20) NMF_HALS_CASE(2, 24) NMF_HALS_CASE(2, 28) NMF_HALS_CASE(2, 32)
+            default: break;
+        }
+    } else {
+        switch (pick(kSlots4, need)) {
+            NMF_HALS_CASE(4, 2) NMF_HALS_CASE(4, 3) NMF_HALS_CASE(4, 4) NMF_HALS_CASE(4, 5) NMF_HALS_CASE(4, 6) NMF_HALS_CASE(4, 7) NMF_HALS_CASE(4, 8) NMF_HALS_CASE(4, 9) NMF_HALS_CASE(4, 10) NMF_HALS_CASE(4, 11) NMF_HALS_CASE(4, 12) NMF_HALS_CASE(4, 13) NMF_HALS_CASE(4, 14) NMF_HALS_CASE(4, 15) NMF_HALS_CASE(4, 16) NMF_HALS_CASE(4, 20) NMF_HALS_CASE(4, 24) NMF_HALS_CASE(4, 28) NMF_HALS_CASE(4, 32)
+            default: break;
+        }
+    }
+#undef NMF_HALS_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int hals_w_num_ctas(int64_t m, int r) {
+    const int T = pick_lanes(m, r);
+    const int64_t per_cta = kThreadsPerCta / T;
+    return (int)((m + per_cta - 1) / per_cta);
+}
+
+cudaError_t launch_hals_h(int64_t n, int64_t ldh, int r, int rs, const float *A,
+                          const float *G, const float *H_in, float *H_out, int sweeps,
+                          const HEpilogue &ep, cudaStream_t st) {
+    WEpilogue none{};
+    return dispatch<0>(n, r, ldh, A, G, rs, H_in, H_out, sweeps, ep, none, st);
+}
+
+cudaError_t launch_hals_w(int64_t m, int r, int rs, const float *C, const float *D,
+                          const float *W_in, float *W_out, int sweeps, const WEpilogue &ep,
+                          cudaStream_t st) {
+    HEpilogue none{};
+    return dispatch<1>(m, r, rs, C, D, rs, W_in, W_out, sweeps, none, ep, st);
+}
+
+}  // namespace nmfg

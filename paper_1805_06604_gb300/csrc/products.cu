@@ -1,0 +1,399 @@
+// products.cu -- the two X products of every outer iteration, FP32 on CUDA
+// cores:
+//   A = W_y^T X   (r x n), the W(:,k)^T X term of the HALS closed form (Sec. 1)
+//   C = X H_y^T   (m x r), the X H^T term of Remark 1 / the W-update
+// Both stream X once.  X is m x ldx row-major with ldx a multiple of 8 (the
+// library pads its copy with zeros), W/C are m x rs, H/A are r x ldh.
+//
+// Tiles are staged global -> shared with cp.async (16-byte, L1-bypassing)
+// through a 3-stage ring.  Sums are compensated: every 32-deep stage is
+// accumulated in FP32, and the stage sums (and the split-K partials) are
+// combined with Kahan's correction, which keeps the products within a few
+// units in the last place of the exact value for the sum lengths met here.  A uses a deterministic split-K over the rows of
+// X: every split writes its partial tile, and the last split of a column
+// tile to finish (atomic ticket) adds the partials in split order.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace nmfg {
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kStages = 3;
+constexpr int BK = 32;          // reduction depth per stage
+constexpr int PADK = BK + 4;    // smem row stride (floats), keeps 16-byte rows
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, bool pred) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const int src_bytes = pred ? 16 : 0;   // 0 -> zero fill
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Kahan's compensated addition: (sum, c) absorbs v; sum - c is the result.
+__device__ __forceinline__ void kahan_add(float &sum, float &c, float v) {
+    const float y = v - c;
+    const float t = sum + y;
+    c = (t - sum) - y;
+    sum = t;
+}
+
+// ---------------------------------------------------------------------------
+// C = X H^T.  CTA: BM = 16*TM rows of X, all R = 8*TR columns of C.
+// Thread (tx in 0..7, ty in 0..15) owns rows ty + 16a and columns tx + 8b.
+// ---------------------------------------------------------------------------
+template <int TM, int TR>
+__global__ void __launch_bounds__(kThreads)
+xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
+               const float *__restrict__ H, int64_t ldh, float *__restrict__ C, int rs) {
+    constexpr int BM = 16 * TM;
+    constexpr int R = 8 * TR;
+    extern __shared__ __align__(16) float sm[];
+    float *Xs = sm;                                   // [kStages][BM][PADK]
+    float *Hs = sm + kStages * BM * PADK;             // [kStages][R][PADK]
+
+    const int tid = threadIdx.x;
+    const int tx = tid % 8, ty = tid / 8;
+    const int64_t row0 = (int64_t)blockIdx.x * BM;
+    const int64_t nk = (ldx + BK - 1) / BK;
+
+    auto load_stage = [&](int stage, int64_t kt) {
+        const int64_t k0 = kt * BK;
+        float *xs = Xs + stage * BM * PADK;
+        for (int idx = tid; idx < BM * (BK / 4); idx += kThreads) {
+            const int rr = idx / (BK / 4), c4 = idx % (BK / 4);
+            const int64_t grow = row0 + rr, gcol = k0 + c4 * 4;
+            const bool ok = grow < m && gcol < ldx;
+            cp_async16(xs + rr * PADK + c4 * 4, ok ? X + grow * ldx + gcol : X, ok);
+        }
+        float *hs = Hs + stage * R * PADK;
+        for (int idx = tid; idx < R * (BK / 4); idx += kThreads) {
+            const int kk = idx / (BK / 4), c4 = idx % (BK / 4);
+            const int64_t gcol = k0 + c4 * 4;
+            const bool ok = kk < r && gcol < ldh;
+            cp_async16(hs + kk * PADK + c4 * 4, ok ? H + (int64_t)kk * ldh + gcol : H, ok);
+        }
+    };
+
+    // Compensated accumulation: each 32-deep stage is summed into `blk`, and
+    // the stage sums are added into (acc, comp) with Kahan's correction.
+    float acc[TM][TR], comp[TM][TR];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TR; ++b) acc[a][b] = comp[a][b] = 0.0f;
+
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (s < nk) load_stage(s, s);
+        cp_async_commit();
+    }
+
+    for (int64_t kt = 0; kt < nk; ++kt) {
+        cp_async_wait<kStages - 2>();
+        __syncthreads();
+        const int64_t nxt = kt + kStages - 1;
+        if (nxt < nk) load_stage((int)(nxt % kStages), nxt);
+        cp_async_commit();
+
+        const float *xs = Xs + (kt % kStages) * BM * PADK;
+        const float *hs = Hs + (kt % kStages) * R * PADK;
+        float blk[TM][TR];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TR; ++b) blk[a][b] = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 4) {
+            float4 xv[TM], hv[TR];
+#pragma unroll
+            for (int a = 0; a < TM; ++a)
+                xv[a] = *reinterpret_cast<const float4 *>(xs + (ty + 16 * a) * PADK + kk);
+#pragma unroll
+            for (int b = 0; b < TR; ++b)
+                hv[b] = *reinterpret_cast<const float4 *>(hs + (tx + 8 * b) * PADK + kk);
+#pragma unroll
+            for (int a = 0; a < TM; ++a)
+#pragma unroll
+                for (int b = 0; b < TR; ++b) {
+                    blk[a][b] = fmaf(xv[a].x, hv[b].x, blk[a][b]);
+                    blk[a][b] = fmaf(xv[a].y, hv[b].y, blk[a][b]);
+                    blk[a][b] = fmaf(xv[a].z, hv[b].z, blk[a][b]);
+                    blk[a][b] = fmaf(xv[a].w, hv[b].w, blk[a][b]);
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TR; ++b) kahan_add(acc[a][b], comp[a][b], blk[a][b]);
+    }
+    cp_async_wait<0>();
+
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+        const int64_t row = row0 + ty + 16 * a;
+        if (row >= m) continue;
+#pragma unroll
+        for (int b = 0; b < TR; ++b) {
+            const int col = tx + 8 * b;
+            if (col < rs) C[row * rs + col] = acc[a][b] - comp[a][b];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A = W^T X.  CTA: BN = 64 columns of X, all R = 8*TR rows of A, rows
+// [i_begin, i_end) of X.  Thread (tx in 0..15, ty in 0..7) owns columns
+// 4tx..4tx+3 and rows ty + 8b of A.
+// ---------------------------------------------------------------------------
+constexpr int BN = 64;
+constexpr int PADN = BN + 4;
+
+template <int TR>
+__global__ void __launch_bounds__(kThreads)
+wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
+               const float *__restrict__ W, int rs, float *__restrict__ A, int64_t lda,
+               int64_t rows_per_split, float *__restrict__ part,
+               unsigned int *__restrict__ tickets) {
+    constexpr int R = 8 * TR;
+    constexpr int PADR = R + 4;
+    extern __shared__ __align__(16) float sm[];
+    float *Xs = sm;                                   // [kStages][BK][PADN]
+    float *Ws = sm + kStages * BK * PADN;             // [kStages][BK][PADR]
+    __shared__ bool am_last;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t col0 = (int64_t)blockIdx.x * BN;
+    const int split = blockIdx.y, nsplit = gridDim.y;
+    const int64_t i_begin = (int64_t)split * rows_per_split;
+    const int64_t i_end = min(m, i_begin + rows_per_split);
+    const int64_t nk = i_end > i_begin ? (i_end - i_begin + BK - 1) / BK : 0;
+
+    auto load_stage = [&](int stage, int64_t kt) {
+        const int64_t i0 = i_begin + kt * BK;
+        float *xs = Xs + stage * BK * PADN;
+        for (int idx = tid; idx < BK * (BN / 4); idx += kThreads) {
+            const int ii = idx / (BN / 4), c4 = idx % (BN / 4);
+            const int64_t grow = i0 + ii, gcol = col0 + c4 * 4;
+            const bool ok = grow < i_end && gcol < ldx;
+            cp_async16(xs + ii * PADN + c4 * 4, ok ? X + grow * ldx + gcol : X, ok);
+        }
+        float *ws = Ws + stage * BK * PADR;
+        for (int idx = tid; idx < BK * (R / 4); idx += kThreads) {
+            const int ii = idx / (R / 4), c4 = idx % (R / 4);
+            const int64_t grow = i0 + ii;
+            const bool ok = grow < i_end && c4 * 4 < rs;
+            cp_async16(ws + ii * PADR + c4 * 4, ok ? W + grow * rs + c4 * 4 : W, ok);
+        }
+    };
+
+    float acc[TR][4], comp[TR][4];
+#pragma unroll
+    for (int b = 0; b < TR; ++b)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[b][c] = comp[b][c] = 0.0f;
+
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (s < nk) load_stage(s, s);
+        cp_async_commit();
+    }
+    for (int64_t kt = 0; kt < nk; ++kt) {
+        cp_async_wait<kStages - 2>();
+        __syncthreads();
+        const int64_t nxt = kt + kStages - 1;
+        if (nxt < nk) load_stage((int)(nxt % kStages), nxt);
+        cp_async_commit();
+
+        const float *xs = Xs + (kt % kStages) * BK * PADN;
+        const float *ws = Ws + (kt % kStages) * BK * PADR;
+        float blk[TR][4];
+#pragma unroll
+        for (int b = 0; b < TR; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) blk[b][c] = 0.0f;
+#pragma unroll 8
+        for (int ii = 0; ii < BK; ++ii) {
+            const float4 xv = *reinterpret_cast<const float4 *>(xs + ii * PADN + tx * 4);
+#pragma unroll
+            for (int b = 0; b < TR; ++b) {
+                const float w = ws[ii * PADR + ty + 8 * b];
+                blk[b][0] = fmaf(w, xv.x, blk[b][0]);
+                blk[b][1] = fmaf(w, xv.y, blk[b][1]);
+                blk[b][2] = fmaf(w, xv.z, blk[b][2]);
+                blk[b][3] = fmaf(w, xv.w, blk[b][3]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < TR; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) kahan_add(acc[b][c], comp[b][c], blk[b][c]);
+    }
+    cp_async_wait<0>();
+#pragma unroll
+    for (int b = 0; b < TR; ++b)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[b][c] -= comp[b][c];
+
+    if (nsplit == 1) {
+#pragma unroll
+        for (int b = 0; b < TR; ++b) {
+            const int k = ty + 8 * b;
+            if (k >= r) continue;
+            const int64_t j = col0 + tx * 4;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (j + c < lda) A[(int64_t)k * lda + j + c] = acc[b][c];
+        }
+        return;
+    }
+
+    // Split-K: write this split's partial tile, then the last split of the
+    // column tile sums the partials in split order.
+    float *my = part + ((int64_t)blockIdx.x * nsplit + split) * (R * BN);
+#pragma unroll
+    for (int b = 0; b < TR; ++b)
+        *reinterpret_cast<float4 *>(my + (ty + 8 * b) * BN + tx * 4) =
+            make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned int t = atomicAdd(tickets + blockIdx.x, 1u);
+        am_last = (t == (unsigned)nsplit - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    const float *base = part + (int64_t)blockIdx.x * nsplit * (R * BN);
+    for (int e = tid * 4; e < R * BN; e += kThreads * 4) {
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f), c = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < nsplit; ++q) {
+            const float4 v = __ldcg(reinterpret_cast<const float4 *>(base + (int64_t)q * R * BN + e));
+            kahan_add(s.x, c.x, v.x);
+            kahan_add(s.y, c.y, v.y);
+            kahan_add(s.z, c.z, v.z);
+            kahan_add(s.w, c.w, v.w);
+        }
+        s.x -= c.x;
+        s.y -= c.y;
+        s.z -= c.z;
+        s.w -= c.w;
+        const int k = e / BN;
+        const int64_t j = col0 + e % BN;
+        if (k < r) {
+            const float vv[4] = {s.x, s.y, s.z, s.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (j + c < lda) A[(int64_t)k * lda + j + c] = vv[c];
+        }
+    }
+    if (tid == 0) tickets[blockIdx.x] = 0u;
+}
+
+template <int TR>
+cudaError_t wtx_launch(const float *X, int64_t m, int64_t ldx, int r, const float *W, int rs,
+                       float *A, int64_t lda, int nsplit, int64_t rows_per_split, float *part,
+                       unsigned int *tickets, cudaStream_t st) {
+    constexpr int R = 8 * TR;
+    const size_t smem = sizeof(float) * (size_t)kStages * BK * (PADN + R + 4);
+    auto kern = wtx_f32_kernel<TR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((lda + BN - 1) / BN), (unsigned)nsplit);
+    kern<<<grid, kThreads, smem, st>>>(X, m, ldx, r, W, rs, A, lda, rows_per_split, part,
+                                       tickets);
+    return cudaGetLastError();
+}
+
+template <int TM, int TR>
+cudaError_t xht_launch(const float *X, int64_t m, int64_t ldx, int r, const float *H,
+                       int64_t ldh, float *C, int rs, cudaStream_t st) {
+    constexpr int BM = 16 * TM;
+    constexpr int R = 8 * TR;
+    const size_t smem = sizeof(float) * (size_t)kStages * (BM + R) * PADK;
+    auto kern = xht_f32_kernel<TM, TR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((m + BM - 1) / BM);
+    kern<<<grid, kThreads, smem, st>>>(X, m, ldx, r, H, ldh, C, rs);
+    return cudaGetLastError();
+}
+
+struct WtxPlan {
+    int nsplit;
+    int64_t rows_per_split;
+    int64_t tiles;
+};
+
+WtxPlan plan_wtx(int64_t m, int64_t lda) {
+    WtxPlan p;
+    p.tiles = (lda + BN - 1) / BN;
+    int64_t want = (3 * kNumSMs + p.tiles - 1) / p.tiles;     // ~3 CTAs per SM
+    int64_t max_split = (m + 8 * BK - 1) / (8 * BK);         // >= 256 rows per split
+    if (want > max_split) want = max_split;
+    if (want < 1) want = 1;
+    if (want > 64) want = 64;
+    p.rows_per_split = ((m + want - 1) / want + BK - 1) / BK * BK;
+    p.nsplit = (int)((m + p.rows_per_split - 1) / p.rows_per_split);
+    if (p.nsplit < 1) p.nsplit = 1;
+    return p;
+}
+
+}  // namespace
+
+size_t wtx_ws_bytes(int64_t m, int64_t lda, int r) {
+    const WtxPlan p = plan_wtx(m, lda);
+    const int R = 8 * ((r + 7) / 8);
+    if (p.nsplit == 1) return 256;
+    return sizeof(float) * (size_t)p.tiles * p.nsplit * R * BN;
+}
+
+int64_t wtx_num_tickets(int64_t lda) { return (lda + BN - 1) / BN; }
+
+cudaError_t launch_wtx_f32(const float *X, int64_t m, int64_t lda, int64_t ldx, int r,
+                           const float *W, int rs, float *A, void *ws, unsigned int *tickets,
+                           cudaStream_t st) {
+    const WtxPlan p = plan_wtx(m, lda);
+    float *part = static_cast<float *>(ws);
+    switch ((r + 7) / 8) {
+#define NMF_WTX_CASE(TRV)                                                                     \
+    case TRV:                                                                                 \
+        return wtx_launch<TRV>(X, m, ldx, r, W, rs, A, lda, p.nsplit, p.rows_per_split, part, \
+                               tickets, st);
+        NMF_WTX_CASE(1) NMF_WTX_CASE(2) NMF_WTX_CASE(3) NMF_WTX_CASE(4)
+        NMF_WTX_CASE(5) NMF_WTX_CASE(6) NMF_WTX_CASE(7) NMF_WTX_CASE(8)
+        NMF_WTX_CASE(9) NMF_WTX_CASE(10) NMF_WTX_CASE(11) NMF_WTX_CASE(12)
+        NMF_WTX_CASE(13) NMF_WTX_CASE(14) NMF_WTX_CASE(15) NMF_WTX_CASE(16)
+#undef NMF_WTX_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_xht_f32(const float *X, int64_t m, int64_t ldx, int r, const float *H,
+                           int64_t ldh, float *C, int rs, cudaStream_t st) {
+    // Two CTAs per SM worth of row tiles when m allows it; else 32-row tiles.
+    const bool big = m >= 2LL * kNumSMs * 64;
+    switch ((r + 7) / 8) {
+#define NMF_XHT_CASE(TRV)                                                           \
+    case TRV:                                                                       \
+        return big ? xht_launch<4, TRV>(X, m, ldx, r, H, ldh, C, rs, st)            \
+                   : xht_launch<2, TRV>(X, m, ldx, r, H, ldh, C, rs, st);
+        NMF_XHT_CASE(1) NMF_XHT_CASE(2) NMF_XHT_CASE(3) NMF_XHT_CASE(4)
+        NMF_XHT_CASE(5) NMF_XHT_CASE(6) NMF_XHT_CASE(7) NMF_XHT_CASE(8)
+        NMF_XHT_CASE(9) NMF_XHT_CASE(10) NMF_XHT_CASE(11) NMF_XHT_CASE(12)
+        NMF_XHT_CASE(13) NMF_XHT_CASE(14) NMF_XHT_CASE(15) NMF_XHT_CASE(16)
+#undef NMF_XHT_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace nmfg

@@ -1,0 +1,373 @@
+// small.cu -- the O((m+n) r^2) and O(mn)-once kernels of an outer iteration.
+//
+//  * ||X||_F^2 (Remark 1's constant term), FP64, once at creation.
+//  * Grams G = W^T W and D = H H^T (the W(:,k)^T W(:,j) coefficients of the
+//    HALS closed form, Sec. 1), split over the long dimension with one
+//    partial per CTA and a fixed-order second pass (deterministic).
+//  * e(0) of Algorithm 2 step 1 through Remark 1.
+//  * The finalize kernel of Algorithm 2 steps 11-20: W_y = W_n + beta (W_n - W)
+//    (optionally projected), H_y for hp = 1, and the accept / restart copies,
+//    driven by the decision the W-sweep kernel left in the device state.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace nmfg {
+namespace {
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int NT>
+__device__ double block_sum_d(double v, double *red) {
+    v = warp_sum_d(v);
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NT / 32; ++i) s += red[i];
+    __syncthreads();
+    return s;   // valid in thread 0
+}
+
+// Kahan's compensated addition: (sum, c) absorbs v; sum - c is the result.
+__device__ __forceinline__ void kahan_add(float &sum, float &c, float v) {
+    const float y = v - c;
+    const float t = sum + y;
+    c = (t - sum) - y;
+    sum = t;
+}
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 2 * kNumSMs;
+
+// ---------------------------------------------------------------- ||X||^2
+__global__ void __launch_bounds__(kRedThreads)
+fro2_partial_kernel(const float *__restrict__ v, int64_t rows, int64_t cols, int64_t ld,
+                    double *__restrict__ part) {
+    __shared__ double red[kRedThreads / 32];
+    double acc = 0.0;
+    const int64_t total = rows * cols;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / cols, j = q % cols;
+        const double x = (double)v[i * ld + j];
+        acc = fma(x, x, acc);
+    }
+    const double s = block_sum_d<kRedThreads>(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void sum_partials_kernel(const double *__restrict__ part, int count,
+                                    double *__restrict__ out) {
+    __shared__ double red[kRedThreads / 32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) acc += part[i];
+    const double s = block_sum_d<kRedThreads>(acc, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// ---------------------------------------------------------------- Grams
+// Partial Gram of a chunk of the long dimension.  Thread (ty, tx) of a
+// 16 x 16 block owns entries (ty + 16a, tx + 16b), a, b < RB (R = 16 RB).
+// ROWS = true: M is N x ldm (entries M[i*ldm + k], k < r), G = M^T M.
+// ROWS = false: M is r x ldm (entries M[k*ldm + i], i < N), G = M M^T.
+constexpr int GBK = 32;
+
+template <int RB, bool ROWS>
+__global__ void __launch_bounds__(256)
+gram_partial_kernel(const float *__restrict__ M, int64_t N, int64_t ldm, int r,
+                    int64_t chunk, float *__restrict__ part, int rs) {
+    constexpr int R = 16 * RB;
+    __shared__ float Ms[GBK][R + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t i0 = (int64_t)blockIdx.x * chunk;
+    const int64_t i1 = min(N, i0 + chunk);
+    // 32-row blocks summed in FP32, blocks combined with Kahan's correction.
+    float acc[RB][RB], comp[RB][RB];
+#pragma unroll
+    for (int a = 0; a < RB; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) acc[a][b] = comp[a][b] = 0.0f;
+
+    for (int64_t ib = i0; ib < i1; ib += GBK) {
+        for (int idx = threadIdx.x; idx < GBK * R; idx += 256) {
+            int ii, k;
+            if (ROWS) {
+                ii = idx / R;
+                k = idx % R;
+            } else {
+                k = idx / GBK;
+                ii = idx % GBK;
+            }
+            const int64_t i = ib + ii;
+            float v = 0.0f;
+            if (i < i1 && k < r) v = ROWS ? M[i * ldm + k] : M[(int64_t)k * ldm + i];
+            Ms[ii][k] = v;
+        }
+        __syncthreads();
+        float blk[RB][RB];
+#pragma unroll
+        for (int a = 0; a < RB; ++a)
+#pragma unroll
+            for (int b = 0; b < RB; ++b) blk[a][b] = 0.0f;
+#pragma unroll 4
+        for (int ii = 0; ii < GBK; ++ii) {
+            float va[RB], vb[RB];
+#pragma unroll
+            for (int a = 0; a < RB; ++a) va[a] = Ms[ii][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < RB; ++b) vb[b] = Ms[ii][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < RB; ++a)
+#pragma unroll
+                for (int b = 0; b < RB; ++b) blk[a][b] = fmaf(va[a], vb[b], blk[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < RB; ++a)
+#pragma unroll
+            for (int b = 0; b < RB; ++b) kahan_add(acc[a][b], comp[a][b], blk[a][b]);
+        __syncthreads();
+    }
+    float *out = part + (int64_t)blockIdx.x * rs * rs;
+#pragma unroll
+    for (int a = 0; a < RB; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const int i = ty + 16 * a, j = tx + 16 * b;
+            if (i < rs && j < rs) out[i * rs + j] = acc[a][b] - comp[a][b];
+        }
+}
+
+__global__ void gram_reduce_kernel(const float *__restrict__ part, int nparts, int rs,
+                                   float *__restrict__ G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rs * rs) return;
+    float s = 0.0f, c = 0.0f;
+    for (int p = 0; p < nparts; ++p) kahan_add(s, c, part[(int64_t)p * rs * rs + e]);
+    G[e] = s - c;
+}
+
+struct GramPlan {
+    int nparts;
+    int64_t chunk;
+};
+
+GramPlan plan_gram(int64_t N) {
+    GramPlan p;
+    int64_t want = (N + 63) / 64;
+    if (want > 2 * kNumSMs) want = 2 * kNumSMs;
+    if (want < 1) want = 1;
+    p.chunk = (N + want - 1) / want;
+    p.nparts = (int)((N + p.chunk - 1) / p.chunk);
+    if (p.nparts < 1) p.nparts = 1;
+    return p;
+}
+
+template <bool ROWS>
+cudaError_t gram_launch(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
+                        void *ws, cudaStream_t st) {
+    const GramPlan p = plan_gram(N);
+    float *part = static_cast<float *>(ws);
+    const int rb = (r + 15) / 16;
+    switch (rb) {
+#define NMF_GRAM_CASE(RBV)                                                                   \
+    case RBV:                                                                                \
+        gram_partial_kernel<RBV, ROWS><<<p.nparts, 256, 0, st>>>(M, N, ldm, r, p.chunk, part, \
+                                                                 rs);                        \
+        break;
+        NMF_GRAM_CASE(1) NMF_GRAM_CASE(2) NMF_GRAM_CASE(3) NMF_GRAM_CASE(4)
+        NMF_GRAM_CASE(5) NMF_GRAM_CASE(6) NMF_GRAM_CASE(7) NMF_GRAM_CASE(8)
+#undef NMF_GRAM_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    gram_reduce_kernel<<<(rs * rs + 255) / 256, 256, 0, st>>>(part, p.nparts, rs, G);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- e(0)
+// Per row i of W: <w_i, c_i> and w_i^T D w_i (FP32 inner products of length
+// r, accumulated across rows in FP64); one partial pair per CTA.
+__global__ void __launch_bounds__(256)
+err_rows_kernel(int64_t m, int r, int rs, const float *__restrict__ W,
+                const float *__restrict__ C, const float *__restrict__ D,
+                ErrPartial *__restrict__ part) {
+    extern __shared__ float Ds[];   // rs x rs
+    __shared__ double red[256 / 32];
+    for (int e = threadIdx.x; e < rs * rs; e += blockDim.x) Ds[e] = D[e];
+    __syncthreads();
+    double cross = 0.0, quad = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float *w = W + i * rs;
+        const float *c = C + i * rs;
+        for (int k = 0; k < r; ++k) {
+            float dw = 0.0f;
+            for (int j = 0; j < r; ++j) dw = fmaf(Ds[k * rs + j], w[j], dw);
+            cross = fma((double)w[k], (double)c[k], cross);
+            quad = fma((double)w[k], (double)dw, quad);
+        }
+    }
+    const double cs = block_sum_d<256>(cross, red);
+    const double qs = block_sum_d<256>(quad, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x].cross = cs;
+        part[blockIdx.x].quad = qs;
+    }
+}
+
+__global__ void init_state_kernel(const ErrPartial *__restrict__ part, int nparts,
+                                  const double *__restrict__ fro2, DevState *__restrict__ s,
+                                  double beta0) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double c = 0.0, q = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+        c += part[p].cross;
+        q += part[p].quad;
+    }
+    const double f = *fro2;
+    const double e2 = f - 2.0 * c + q;
+    const double e = sqrt(e2 > 0.0 ? e2 : 0.0);
+    s->fro2 = f;
+    s->e_last = e;
+    s->e_prev = e;
+    s->e_k = e;
+    s->beta = beta0;
+    s->beta_bar = 1.0;
+    s->beta_prev = beta0;
+    s->beta_used = beta0;
+    s->k = 0;
+    s->accepted = 1;
+    s->status = isfinite(e2) ? 0 : (int)NMF_ENONFINITE;
+}
+
+// ---------------------------------------------------------------- finalize
+// W part: q < m*rs, H part: q < r*ldh.  Padded entries are zero everywhere
+// and stay zero.
+__global__ void __launch_bounds__(256)
+finalize_kernel(int64_t nw, int64_t nh, float *__restrict__ W, float *__restrict__ H,
+                float *__restrict__ Wy, float *__restrict__ Hy, const float *__restrict__ Wn,
+                const float *__restrict__ Hn, const float *__restrict__ Hw,
+                const DevState *__restrict__ state, DevParams p) {
+    const int acc = state->accepted;
+    const float beta = (float)state->beta_used;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nw + nh; q += stride) {
+        if (q < nw) {
+            if (acc) {
+                const float wold = W[q], wn = Wn[q];
+                float wy = fmaf(beta, wn - wold, wn);          // step 11
+                if (p.project_w) wy = fmaxf(wy, 0.0f);
+                W[q] = wn;                                     // step 19
+                Wy[q] = wy;
+            } else {
+                Wy[q] = W[q];                                  // step 17
+            }
+        } else {
+            const int64_t h = q - nw;
+            if (acc) {
+                const float hold = H[h], hn = Hn[h];
+                float hy;
+                if (p.hp == 1) hy = fmaf(beta, hn - hold, hn); // step 13
+                else hy = Hw[h];                               // steps 4-9
+                H[h] = hn;
+                Hy[h] = hy;
+            } else {
+                Hy[h] = H[h];
+            }
+        }
+    }
+}
+
+__global__ void nonfinite_kernel(const float *__restrict__ v, int64_t count, int *flag) {
+    int bad = 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+         q += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(v[q]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+}  // namespace
+
+size_t fro2_ws_bytes(int64_t) { return sizeof(double) * kRedBlocks; }
+
+cudaError_t launch_fro2(const float *vals, int64_t rows, int64_t cols, int64_t ld, double *out,
+                        void *ws, cudaStream_t st) {
+    double *part = static_cast<double *>(ws);
+    fro2_partial_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(vals, rows, cols, ld, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_partials_kernel<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, out);
+    return cudaGetLastError();
+}
+
+size_t gram_ws_bytes(int64_t N, int rs) {
+    const GramPlan p = plan_gram(N);
+    return sizeof(float) * (size_t)p.nparts * rs * rs;
+}
+
+cudaError_t launch_gram_rows(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
+                             void *ws, cudaStream_t st) {
+    return gram_launch<true>(M, N, ldm, r, rs, G, ws, st);
+}
+
+cudaError_t launch_gram_cols(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
+                             void *ws, cudaStream_t st) {
+    return gram_launch<false>(M, N, ldm, r, rs, G, ws, st);
+}
+
+int err_rows_num_ctas(int64_t m) {
+    int64_t b = (m + 255) / 256;
+    if (b > 2 * kNumSMs) b = 2 * kNumSMs;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_err_rows(int64_t m, int r, int rs, const float *W, const float *C,
+                            const float *D, ErrPartial *part, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (size_t)rs * rs;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(err_rows_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    err_rows_kernel<<<err_rows_num_ctas(m), 256, smem, st>>>(m, r, rs, W, C, D, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(int64_t m, int r, int rs, const float *W, const float *C,
+                              const float *D, const double *fro2, DevState *state,
+                              double beta0, ErrPartial *partials, cudaStream_t st) {
+    cudaError_t e = launch_err_rows(m, r, rs, W, C, D, partials, st);
+    if (e != cudaSuccess) return e;
+    init_state_kernel<<<1, 32, 0, st>>>(partials, err_rows_num_ctas(m), fro2, state, beta0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(int64_t m, int rs, int r, int64_t ldh, float *W, float *H,
+                            float *Wy, float *Hy, const float *Wn, const float *Hn,
+                            const float *Hw, const DevState *state, DevParams p,
+                            cudaStream_t st) {
+    const int64_t nw = m * rs, nh = (int64_t)r * ldh;
+    int64_t blocks = (nw + nh + 255) / 256;
+    if (blocks > 8 * kNumSMs) blocks = 8 * kNumSMs;
+    finalize_kernel<<<(unsigned)blocks, 256, 0, st>>>(nw, nh, W, H, Wy, Hy, Wn, Hn, Hw, state, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite_scan(const float *v, int64_t count, int *flag, cudaStream_t st) {
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 4 * kNumSMs) blocks = 4 * kNumSMs;
+    if (blocks < 1) blocks = 1;
+    nonfinite_kernel<<<(unsigned)blocks, 256, 0, st>>>(v, count, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace nmfg

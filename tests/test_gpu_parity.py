@@ -1,0 +1,281 @@
+"""CUDA path vs the FP64 oracle, through the C-ABI (libnmf_gb300.so).
+
+Tolerances (FP32 path):
+  * single step from an identical state: every factor within 1e-5 normwise
+    (max |gpu - oracle| / max |oracle|), or 4 kappa 2^-24 when the Grams'
+    condition number kappa puts the FP32 floor above 1e-5 (gpu_helpers);
+    same accept/restart decision;
+  * e(k): |e_gpu^2 - e_orc^2| <= 2e-6 ||X||^2 -- the FP32 products carry a
+    relative error of order sqrt(n) u (u = 2^-24) into <W, X H^T>, and the
+    expanded error of Remark 1 cancels ||X||^2 against 2<W, XH^T>, so the
+    bound is absolute in ||X||^2, not relative in e^2;
+  * after K iterations: the relative error of the returned pair within 1e-4
+    relative of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1805_06604_gb300 import nmf
+from paper_1805_06604_gb300 import workloads as wl
+
+from gpu_helpers import (f32, gpu_kwargs, make_solver, normwise, oracle_X, oracle_params,
+                         single_step)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1805_06604_gb300 import build
+    build.build()
+    O.build()
+    nmf.load()
+
+
+def _check_step(res):
+    g, o = res["gpu"], res["orc"]
+    tol = res["tol"]
+    assert g["acc"] == o["acc"], (g["e"], o["e"], o["scalars"].e_last)
+    assert g["beta"] == pytest.approx(o["beta"], rel=1e-15)
+    for name in ("W", "H", "Wy", "Hy"):
+        err = normwise(g[name], o[name])
+        assert err <= tol, f"{name}: normwise error {err:.3e} > {tol:.2e} (kappa {res['kappa']:.0f})"
+    assert abs(g["e"] ** 2 - o["e"] ** 2) <= 2e-6 * res["fro2"]
+    sg, so = g["scalars"], o["scalars"]
+    assert sg.k == so.k
+    assert sg.beta == pytest.approx(so.beta, rel=1e-14)
+    assert sg.beta_bar == pytest.approx(so.beta_bar, rel=1e-14)
+
+
+@pytest.mark.parametrize("m,n,r,hp,warm", [
+    (300, 220, 12, 3, 0),      # first step
+    (300, 220, 12, 3, 8),      # mid-run: beta > 0, W_y != W
+    (257, 193, 33, 3, 5),      # ragged m, n (n not a multiple of 8), r not a multiple of 4
+    (1000, 700, 50, 3, 6),     # several tiles of every kernel
+    (96, 130, 64, 2, 4),       # hp = 2 (no projection)
+    (200, 150, 10, 1, 6),      # hp = 1 (H extrapolated after the W-update)
+    (130, 77, 1, 3, 3),        # r = 1
+    (150, 140, 128, 3, 2),     # r at the build cap
+])
+def test_single_step_matches_oracle(m, n, r, hp, warm):
+    P = wl.low_rank(m, n, r, seed=m + n + r, noise=0.02)
+    p = oracle_params(P, hp=hp)
+    _check_step(single_step(P, p, warm))
+
+
+def test_single_step_project_w_and_compare_prev():
+    P = wl.low_rank(240, 180, 16, seed=3, noise=0.02)
+    _check_step(single_step(P, oracle_params(P, project_w=1), 6))
+    _check_step(single_step(P, oracle_params(P, compare_prev=1), 6))
+
+
+def test_single_step_after_forced_restart():
+    """A state whose e_last is tiny forces a restart: the GPU must restore
+    W_y = W, H_y = H and apply the shrink branch of Algorithm 3."""
+    P = wl.low_rank(200, 160, 8, seed=4, noise=0.02)
+    p = oracle_params(P)
+    Xo = oracle_X(P)
+    st = O.eahals_init(Xo, P.W0, P.H0, p)
+    O.eahals_run(Xo, st, p, 5)
+    st.s.e_last = 1e-30
+    from gpu_helpers import load_state, state_to_f32
+    st = state_to_f32(st)
+    with make_solver(P, p) as s:
+        load_state(s, st)
+        s.step(1)
+        sc, W, H, Wy, Hy = s.get_state()
+        _, _, ta = s.trace()
+    e_o, _, acc_o = O.eahals_step(Xo, st, p)
+    assert not acc_o and not ta[-1]
+    for a, b in ((W, st.W), (H, st.H), (Wy, st.Wy), (Hy, st.Hy)):
+        assert normwise(a, b) == 0.0
+    assert sc.beta == pytest.approx(st.s.beta, rel=1e-15)
+    assert sc.beta_bar == pytest.approx(st.s.beta_bar, rel=1e-15)
+
+
+@pytest.mark.parametrize("hp", [3, 1])
+def test_k_iterations_relative_error(hp):
+    """K iterations to the noise floor of a noisy low-rank X: the relative
+    error of the returned pair matches the oracle's within 1e-4 relative."""
+    P = wl.low_rank(400, 300, 20, seed=11, noise=0.01)
+    p = oracle_params(P, hp=hp)
+    Xo = oracle_X(P)
+    K = 800
+    st = O.eahals_init(Xo, P.W0, P.H0, p)
+    O.eahals_run(Xo, st, p, K)
+    rel_o = np.linalg.norm(Xo - st.W @ st.H) / np.linalg.norm(Xo)
+    with make_solver(P, p) as s:
+        s.step(K)
+        W, H = s.factors()
+    rel_g = np.linalg.norm(Xo - W.astype(np.float64) @ H) / np.linalg.norm(Xo)
+    assert abs(rel_g - rel_o) <= 1e-4 * rel_o, (rel_g, rel_o)
+
+
+def test_decision_replay_low_rank():
+    """Exactly low-rank X (e_min = 0): the oracle replays the GPU's
+    accept/restart decisions, so both follow the same branch sequence; the
+    per-iteration errors and the final relative error then agree."""
+    P = wl.oracle_scale(0)
+    p = oracle_params(P)
+    Xo = oracle_X(P)
+    K = 200
+    with make_solver(P, p) as s:
+        s.step(K)
+        te_g, tb_g, ta_g = s.trace()
+        W, H = s.factors()
+    st = O.eahals_init(Xo, f32(P.W0), f32(P.H0), p)
+    te_o, tb_o, ta_o = O.eahals_run(Xo, st, p, K, forced=ta_g.astype(np.int8))
+    np.testing.assert_allclose(tb_g, tb_o, rtol=1e-13)
+    np.testing.assert_allclose(te_g, te_o, rtol=1e-3)
+    rel_o = np.linalg.norm(Xo - st.W @ st.H) / np.linalg.norm(Xo)
+    rel_g = np.linalg.norm(Xo - W.astype(np.float64) @ H) / np.linalg.norm(Xo)
+    assert abs(rel_g - rel_o) <= 1e-4 * rel_o + 1e-6, (rel_g, rel_o)
+    # without replay the GPU takes the oracle's own decisions while e(k) is
+    # far from ties
+    _, _, ta_f = O.eahals_run(Xo, O.eahals_init(Xo, f32(P.W0), f32(P.H0), p), p, 40)
+    np.testing.assert_array_equal(ta_g[:40], ta_f)
+
+
+def test_beta0_zero_is_ahals():
+    P = wl.low_rank(220, 170, 9, seed=12, noise=0.02)
+    p = oracle_params(P, beta0=0.0)
+    Xo = oracle_X(P)
+    with make_solver(P, p) as s:
+        s.step(30)
+        W, H = s.factors()
+        _, tb, ta = s.trace()
+    assert np.all(tb == 0.0)
+    Wo, Ho, _ = O.ahals_run(Xo, f32(P.W0), f32(P.H0), p.lw, p.lh, 30)
+    rel_o = np.linalg.norm(Xo - Wo @ Ho) / np.linalg.norm(Xo)
+    rel_g = np.linalg.norm(Xo - W.astype(np.float64) @ H) / np.linalg.norm(Xo)
+    assert abs(rel_g - rel_o) <= 1e-4 * rel_o
+
+
+def _document(seed=5):
+    return wl.document_like(seed=seed, m=3000, n=1500, r=16, mu=4.0, sigma=0.8)
+
+
+def test_csr_single_step_and_k_iterations():
+    P = _document()
+    p = oracle_params(P)
+    _check_step(single_step(P, p, 4))
+    Xo = oracle_X(P)
+    st = O.eahals_init(Xo, P.W0, P.H0, p)
+    O.eahals_run(Xo, st, p, 60)
+    with make_solver(P, p) as s:
+        s.step(60)
+        W, H = s.factors()
+    D = P.dense().astype(np.float64)
+    rel_o = np.linalg.norm(D - st.W @ st.H) / np.linalg.norm(D)
+    rel_g = np.linalg.norm(D - W.astype(np.float64) @ H) / np.linalg.norm(D)
+    assert abs(rel_g - rel_o) <= 1e-4 * rel_o, (rel_g, rel_o)
+
+
+def test_zero_column_is_skipped():
+    """A zero column of W_y gives G_kk = 0: that row of H keeps its value."""
+    P = wl.low_rank(120, 90, 6, seed=13, noise=0.02)
+    P.W0[:, 2] = 0.0
+    p = oracle_params(P)
+    _check_step(single_step(P, p, 0))
+
+
+def test_deterministic_and_resume_bit_identical():
+    P = wl.low_rank(500, 350, 24, seed=14, noise=0.01)
+    p = oracle_params(P)
+    with make_solver(P, p) as a, make_solver(P, p) as b:
+        a.step(25)
+        b.step(10)
+        state = b.get_state()
+        with make_solver(P, p) as c:
+            c.set_state(*state)
+            c.step(15)
+            Wa, Ha = a.factors()
+            Wc, Hc = c.factors()
+            np.testing.assert_array_equal(Wa, Wc)
+            np.testing.assert_array_equal(Ha, Hc)
+            ea, _, _ = a.trace()
+            ec, _, _ = c.trace()
+            np.testing.assert_array_equal(ea[10:25], ec[10:25])
+
+
+def test_solve_stops_at_target():
+    P = wl.low_rank(300, 200, 10, seed=15, noise=0.0)
+    p = oracle_params(P)
+    with make_solver(P, p) as s:
+        res = s.solve(2000, target_relerr=1e-3, check_every=10)
+        assert res.reached == 1 and res.relerr <= 1e-3
+        assert res.iters % 10 == 0 and res.iters < 2000
+
+
+@pytest.mark.parametrize("case", ["nan_x", "neg_w0", "rank_cap", "bad_hp", "bad_gamma",
+                                  "csr_col", "csr_rowptr"])
+def test_invalid_inputs_are_rejected(case):
+    P = wl.low_rank(40, 30, 4, seed=16, noise=0.0)
+    X, W0, H0 = f32(P.X), f32(P.W0), f32(P.H0)
+    kw = {}
+    expect = nmf.NMF_EINVAL
+    r = P.r
+    csr = None
+    if case == "nan_x":
+        X = X.copy()
+        X[3, 4] = np.nan
+        expect = nmf.NMF_ENONFINITE
+    elif case == "neg_w0":
+        W0 = W0.copy()
+        W0[1, 1] = -1.0
+    elif case == "rank_cap":
+        r = 129
+        W0 = np.ones((40, r), np.float32)
+        H0 = np.ones((r, 30), np.float32)
+        expect = nmf.NMF_ENOTSUP
+    elif case == "bad_hp":
+        kw = dict(hp=4)
+    elif case == "bad_gamma":
+        kw = dict(gamma=1.001, gamma_bar=1.005)
+    else:
+        rp, ci, v = wl.csr_from_dense(X)
+        ci = ci.copy()
+        rp = rp.copy()
+        if case == "csr_col":
+            ci[5] = 30
+        else:
+            rp[10] = rp[11] + 1
+        csr = (rp, ci, v)
+    with pytest.raises(nmf.NmfError) as ei:
+        if csr is None:
+            nmf.Solver(X, r, W0, H0, **kw)
+        else:
+            nmf.Solver(None, r, W0, H0, csr=csr, m=40, n=30, **kw)
+    assert ei.value.status == expect
+
+
+def test_device_inputs_and_stream():
+    import torch
+    P = wl.low_rank(260, 190, 14, seed=17, noise=0.01)
+    p = oracle_params(P)
+    st = torch.cuda.Stream()
+    X = torch.from_numpy(f32(P.X)).cuda()
+    W0 = torch.from_numpy(f32(P.W0)).cuda()
+    H0 = torch.from_numpy(f32(P.H0)).cuda()
+    with nmf.Solver(X, P.r, W0, H0, stream=st, **gpu_kwargs(p)) as s, make_solver(P, p) as ref:
+        s.step(12)
+        ref.step(12)
+        Wd = torch.empty((P.m, P.r), device="cuda")
+        Hd = torch.empty((P.r, P.n), device="cuda")
+        nmf.nmf_get_factors(s.h, Wd, Hd)
+        Wr, Hr = ref.factors()
+        np.testing.assert_array_equal(Wd.cpu().numpy(), Wr)
+        np.testing.assert_array_equal(Hd.cpu().numpy(), Hr)
+
+
+def test_profile_phases_advances_like_step():
+    P = wl.low_rank(300, 250, 16, seed=18, noise=0.01)
+    p = oracle_params(P)
+    with make_solver(P, p) as a, make_solver(P, p) as b:
+        ms = a.profile_phases(4)
+        b.step(4)
+        assert set(ms) == set(nmf.PHASES) and all(v > 0 for v in ms.values())
+        np.testing.assert_array_equal(a.factors()[0], b.factors()[0])
