@@ -73,15 +73,18 @@ struct nmf_handle {
     int32_t *rowidx = nullptr;
     float *cval = nullptr;
     float *Ht = nullptr;                         // n x rs transpose of H_y' (CSR path)
+    float *carry = nullptr;                      // chunk partials of the CSR products
     // factors and products
     float *W = nullptr, *H = nullptr, *Wy = nullptr, *Hy = nullptr;
     float *Wn = nullptr, *Hn = nullptr, *Hw = nullptr;
     float *A = nullptr, *C = nullptr, *G = nullptr, *D = nullptr;
+    float *C_lo = nullptr, *D_lo = nullptr;      // low parts for the Remark 1 terms
     double *fro2 = nullptr;
     DevState *state = nullptr;
     ErrPartial *partials = nullptr;
     unsigned int *counter = nullptr;
-    unsigned int *tickets = nullptr;
+    unsigned int *tickets = nullptr;             // split-K tickets of W^T X
+    unsigned int *xtickets = nullptr;            // split-K tickets of X H^T
     void *ws = nullptr;
     size_t ws_bytes = 0;
     int *flag = nullptr;
@@ -101,8 +104,10 @@ void free_handle(nmf_handle *h) {
     if (!h) return;
     if (h->exec) cudaGraphExecDestroy(h->exec);
     void *ptrs[] = {h->X, h->rowptr, h->colidx, h->val, h->colptr, h->rowidx, h->cval, h->Ht,
+                    h->carry,
                     h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn, h->Hw, h->A, h->C, h->G, h->D,
-                    h->fro2, h->state, h->partials, h->counter, h->tickets, h->ws, h->flag,
+                    h->C_lo, h->D_lo,
+                    h->fro2, h->state, h->partials, h->counter, h->tickets, h->xtickets, h->ws, h->flag,
                     h->tr_e, h->tr_beta, h->tr_acc};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -133,8 +138,8 @@ DevParams dev_params(const nmf_handle *h) {
 // X products for the current layout.
 cudaError_t enqueue_wtx(nmf_handle *h, const float *Wsrc, cudaStream_t st) {
     if (h->is_csr)
-        return launch_wtx_csc(h->colptr, h->rowidx, h->cval, h->n, h->r, h->rs, Wsrc, h->A, h->ld,
-                              st);
+        return launch_wtx_csc(h->colptr, h->rowidx, h->cval, h->n, h->nnz, h->r, h->rs, Wsrc, h->A,
+                              h->ld, h->carry, st);
     return launch_wtx_f32(h->X, h->m, h->ld, h->ld, h->r, Wsrc, h->rs, h->A, h->ws, h->tickets,
                           st);
 }
@@ -143,9 +148,11 @@ cudaError_t enqueue_xht(nmf_handle *h, const float *Hsrc, cudaStream_t st) {
     if (h->is_csr) {
         cudaError_t e = launch_transpose_h(Hsrc, h->r, h->n, h->ld, h->Ht, h->rs, st);
         if (e != cudaSuccess) return e;
-        return launch_xht_csr(h->rowptr, h->colidx, h->val, h->m, h->r, h->rs, h->Ht, h->C, st);
+        return launch_xht_csr(h->rowptr, h->colidx, h->val, h->m, h->nnz, h->r, h->rs, h->Ht, h->C,
+                              h->carry, st);
     }
-    return launch_xht_f32(h->X, h->m, h->ld, h->r, Hsrc, h->ld, h->C, h->rs, st);
+    return launch_xht_f32(h->X, h->m, h->ld, h->r, Hsrc, h->ld, h->C, h->C_lo, h->rs, h->ws,
+                          h->xtickets, st);
 }
 
 // One outer iteration of Algorithm 2, enqueued on st.  When ev != nullptr,
@@ -173,11 +180,13 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
     NMF_STEP(launch_hals_h(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hy, h->Hn, h->lh, hep, st));
     const float *Hused = h->p.hp >= 2 ? h->Hw : h->Hn;
     NMF_STEP(mark(NMF_PHASE_GRAM_H));
-    NMF_STEP(launch_gram_cols(Hused, h->n, h->ld, h->r, h->rs, h->D, h->ws, st));
+    NMF_STEP(launch_gram_cols(Hused, h->n, h->ld, h->r, h->rs, h->D, h->D_lo, h->ws, st));
     NMF_STEP(mark(NMF_PHASE_XHT));
     NMF_STEP(enqueue_xht(h, Hused, st));
     NMF_STEP(mark(NMF_PHASE_HALS_W));
     WEpilogue wep{};
+    wep.C_lo = h->C_lo;
+    wep.D_lo = h->D_lo;
     wep.partials = h->partials;
     wep.counter = h->counter;
     wep.state = h->state;
@@ -415,6 +424,7 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     NMF_TRYC(dalloc(&h->Wy, m * rs));
     NMF_TRYC(dalloc(&h->Wn, m * rs));
     NMF_TRYC(dalloc(&h->C, m * rs));
+    NMF_TRYC(dalloc(&h->C_lo, m * rs));
     NMF_TRYC(dalloc(&h->H, r * ld));
     NMF_TRYC(dalloc(&h->Hy, r * ld));
     NMF_TRYC(dalloc(&h->Hn, r * ld));
@@ -422,6 +432,7 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     NMF_TRYC(dalloc(&h->A, r * ld));
     NMF_TRYC(dalloc(&h->G, rs * rs));
     NMF_TRYC(dalloc(&h->D, rs * rs));
+    NMF_TRYC(dalloc(&h->D_lo, rs * rs));
     NMF_TRYC(dalloc(&h->fro2, 1));
     NMF_TRYC(dalloc(&h->state, 1));
     NMF_TRYC(dalloc(&h->flag, 1));
@@ -429,22 +440,25 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     NMF_TRYC(dalloc(&h->partials, npart));
     NMF_TRYC(dalloc(&h->counter, 1));
     NMF_TRYC(dalloc(&h->tickets, wtx_num_tickets(ld)));
+    NMF_TRYC(dalloc(&h->xtickets, xht_num_tickets(m)));
     NMF_TRYC(cudaHostAlloc((void **)&h->h_state, sizeof(DevState), cudaHostAllocDefault));
     size_t ws = std::max(gram_ws_bytes(m, (int)rs), gram_ws_bytes(n, (int)rs));
     ws = std::max(ws, fro2_ws_bytes(m * ld));
-    if (!h->is_csr) ws = std::max(ws, wtx_ws_bytes(m, ld, r));
+    if (!h->is_csr) ws = std::max({ws, wtx_ws_bytes(m, ld, r), xht_ws_bytes(m, ld, r)});
     h->ws_bytes = ws;
     NMF_TRYC(cudaMalloc(&h->ws, ws));
 
     cudaStream_t st = h->st;
-    for (void *q : {(void *)h->W, (void *)h->Wy, (void *)h->Wn, (void *)h->C})
+    for (void *q : {(void *)h->W, (void *)h->Wy, (void *)h->Wn, (void *)h->C, (void *)h->C_lo})
         NMF_TRYC(cudaMemsetAsync(q, 0, sizeof(float) * m * rs, st));
     for (void *q : {(void *)h->H, (void *)h->Hy, (void *)h->Hn, (void *)h->Hw, (void *)h->A})
         NMF_TRYC(cudaMemsetAsync(q, 0, sizeof(float) * r * ld, st));
     NMF_TRYC(cudaMemsetAsync(h->G, 0, sizeof(float) * rs * rs, st));
     NMF_TRYC(cudaMemsetAsync(h->D, 0, sizeof(float) * rs * rs, st));
+    NMF_TRYC(cudaMemsetAsync(h->D_lo, 0, sizeof(float) * rs * rs, st));
     NMF_TRYC(cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), st));
     NMF_TRYC(cudaMemsetAsync(h->tickets, 0, sizeof(unsigned int) * wtx_num_tickets(ld), st));
+    NMF_TRYC(cudaMemsetAsync(h->xtickets, 0, sizeof(unsigned int) * xht_num_tickets(m), st));
     NMF_TRYC(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
     NMF_TRYC(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
 
@@ -479,6 +493,7 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
         NMF_TRYC(dalloc(&h->rowidx, nnz));
         NMF_TRYC(dalloc(&h->cval, nnz));
         NMF_TRYC(dalloc(&h->Ht, n * rs));
+        NMF_TRYC(dalloc(&h->carry, csr_carry_floats(nnz, (int)rs)));
         NMF_TRYC(cudaMemsetAsync(h->Ht, 0, sizeof(float) * n * rs, st));
         NMF_TRYC(cudaMemcpyAsync(h->rowptr, rp.data(), sizeof(int64_t) * (m + 1),
                                  cudaMemcpyHostToDevice, st));
@@ -517,10 +532,10 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     }
 
     // e(0) = ||X - W H||_F via Remark 1 (Algorithm 2 step 1).
-    NMF_TRYC(launch_gram_cols(h->H, n, ld, r, (int)rs, h->D, h->ws, st));
+    NMF_TRYC(launch_gram_cols(h->H, n, ld, r, (int)rs, h->D, h->D_lo, h->ws, st));
     NMF_TRYC(enqueue_xht(h, h->H, st));
-    NMF_TRYC(launch_init_state(m, r, (int)rs, h->W, h->C, h->D, h->fro2, h->state, p.beta0,
-                               h->partials, st));
+    NMF_TRYC(launch_init_state(m, r, (int)rs, h->W, h->C, h->C_lo, h->D, h->D_lo, h->fro2,
+                               h->state, p.beta0, h->partials, st));
     NMF_TRYC(cudaStreamSynchronize(st));
 
     int64_t cap = p.trace_capacity > 0 ? p.trace_capacity : 4096;
@@ -560,9 +575,10 @@ nmf_status nmf_get_info(nmf_handle *h, nmf_info *info) {
     info->lw = h->lw;
     info->lh = h->lh;
     info->device_status = d.status;
-    // gram W (2) + W^T X (1, or 1 for CSC) + H sweeps (1) + gram H (2) +
-    // X H^T (1; CSR adds the H transpose) + W sweeps (1) + finalize (1)
-    info->launches_per_iter = h->is_csr ? 10 : 9;
+    // dense: gram W (2) + W^T X (1) + H sweeps (1) + gram H (2) + X H^T (1) +
+    // W sweeps (1) + finalize (1); CSR: each product is 2 kernels (+ a
+    // memset) and X H^T adds the H transpose.
+    info->launches_per_iter = h->is_csr ? 12 : 9;
     return NMF_OK;
 }
 

@@ -45,8 +45,9 @@ struct DevTrace {
     long long cap;
 };
 
-// Error reduction partials of one W-sweep launch (Remark 1):
-// cross = <W_n, C>, quad = <W_n^T W_n, D> accumulated per CTA in FP64.
+// Error reduction partials of one W-sweep launch (Remark 1 in residual
+// form, ||X - W H||^2 = ||X||^2 - cross + quad): cross = <W_n, C>,
+// quad = <W_n, W_n D - C>, accumulated per CTA in FP64.
 struct ErrPartial {
     double cross;
     double quad;
@@ -76,8 +77,9 @@ cudaError_t launch_fro2(const float *vals, int64_t rows, int64_t cols, int64_t l
 size_t gram_ws_bytes(int64_t N, int rs);
 cudaError_t launch_gram_rows(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
                              void *ws, cudaStream_t st);
+// The Gram of H is accumulated error-free and returned as G + G_lo.
 cudaError_t launch_gram_cols(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
-                             void *ws, cudaStream_t st);
+                             float *G_lo, void *ws, cudaStream_t st);
 
 // Dense products, FP32 on CUDA cores.  A = W^T X (r x ld), C = X H^T (m x rs).
 // The split-K of A needs ws (partial tiles) and wtx_num_tickets() zeroed
@@ -87,8 +89,11 @@ int64_t wtx_num_tickets(int64_t ld);
 cudaError_t launch_wtx_f32(const float *X, int64_t m, int64_t lda, int64_t ldx, int r,
                            const float *W, int rs, float *A, void *ws, unsigned int *tickets,
                            cudaStream_t st);
+size_t xht_ws_bytes(int64_t m, int64_t ldx, int r);
+int64_t xht_num_tickets(int64_t m);
 cudaError_t launch_xht_f32(const float *X, int64_t m, int64_t ldx, int r, const float *H,
-                           int64_t ldh, float *C, int rs, cudaStream_t st);
+                           int64_t ldh, float *C, float *C_lo, int rs, void *ws,
+                           unsigned int *tickets, cudaStream_t st);
 
 // HALS sweeps.  H side: columns of H independent given A and G.  W side:
 // rows of W independent given C and D.
@@ -99,6 +104,8 @@ struct HEpilogue {            // optional fused work after the H sweeps
     int hp;
 };
 struct WEpilogue {            // optional fused work after the W sweeps
+    const float *C_lo;        // low parts of C = X H^T and D = H H^T (error terms)
+    const float *D_lo;
     ErrPartial *partials;     // one per CTA, or null (no error terms)
     unsigned int *counter;    // last-CTA ticket (zero between launches)
     DevState *state;          // decision + Algorithm 3, or null
@@ -120,23 +127,29 @@ cudaError_t launch_finalize(int64_t m, int rs, int r, int64_t ldh, float *W, flo
                             const float *Hw, const DevState *state, DevParams p,
                             cudaStream_t st);
 
-// Remark 1 error terms of (W, C = X H^T, D = H H^T), one partial per CTA.
+// Remark 1 error terms of (W, C = X H^T, D = H H^T) given as hi + lo pairs,
+// one partial per CTA.
 int err_rows_num_ctas(int64_t m);
 cudaError_t launch_err_rows(int64_t m, int r, int rs, const float *W, const float *C,
-                            const float *D, ErrPartial *part, cudaStream_t st);
+                            const float *C_lo, const float *D, const float *D_lo,
+                            ErrPartial *part, cudaStream_t st);
 
 // e(0) (Algorithm 2 step 1) and the initial Algorithm 3 values.
 cudaError_t launch_init_state(int64_t m, int r, int rs, const float *W, const float *C,
-                              const float *D, const double *fro2, DevState *state,
-                              double beta0, ErrPartial *partials, cudaStream_t st);
+                              const float *C_lo, const float *D, const float *D_lo,
+                              const double *fro2, DevState *state, double beta0,
+                              ErrPartial *partials, cudaStream_t st);
 
 // Sparse X (csr.cu): C = X H^T from CSR with Ht = H^T (n x rs); A = W^T X
-// from the CSC copy; H (r x ldh) -> Ht.
+// from the CSC copy; H (r x ldh) -> Ht.  `carry` holds csr_carry_floats()
+// floats of per-chunk partials.
+size_t csr_carry_floats(int64_t nnz, int rs);
 cudaError_t launch_xht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
-                           int64_t m, int r, int rs, const float *Ht, float *C, cudaStream_t st);
+                           int64_t m, int64_t nnz, int r, int rs, const float *Ht, float *C,
+                           float *carry, cudaStream_t st);
 cudaError_t launch_wtx_csc(const int64_t *colptr, const int32_t *rowidx, const float *val,
-                           int64_t n, int r, int rs, const float *W, float *A, int64_t lda,
-                           cudaStream_t st);
+                           int64_t n, int64_t nnz, int r, int rs, const float *W, float *A,
+                           int64_t lda, float *carry, cudaStream_t st);
 cudaError_t launch_transpose_h(const float *H, int r, int64_t n, int64_t ldh, float *Ht, int rs,
                                cudaStream_t st);
 

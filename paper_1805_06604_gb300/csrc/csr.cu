@@ -1,12 +1,17 @@
 // csr.cu -- the two X products for a sparse X (document matrices, Table 2 of
-// Ang & Gillis, arXiv 1805.06604), without atomics:
-//   C = X H_y^T : one warp per row of X (CSR); each nonzero X(i,j) gathers the
-//                 contiguous row j of H_y^T (n x rs, built by transpose_h).
-//   A = W_y^T X : one warp per column of X (CSC = CSR of X^T); each nonzero
-//                 X(i,j) gathers the contiguous row i of W_y (m x rs).
-// Lanes cover the rank dimension (lane, lane+32, ...), so every gather is a
-// coalesced read of one factor row.  Sums run over the stored entries in
-// index order, so results are deterministic.
+// Ang & Gillis, arXiv 1805.06604), without atomics and deterministic:
+//   C = X H_y^T : rows of X (CSR); each nonzero X(i,j) gathers the
+//                 contiguous row j of H_y^T (n x rs, built by transpose_h);
+//   A = W_y^T X : rows of X^T (the CSC copy); each nonzero X(i,j) gathers
+//                 the contiguous row i of W_y (m x rs).
+// Work is split by nonzeros, not by rows: warp c owns the stored entries
+// [c*kChunk, (c+1)*kChunk), so the Zipf-heavy rows of a term-document
+// matrix spread over many warps.  Lanes cover the rank dimension (lane,
+// lane+32, ...), so every gather is one coalesced read of a factor row.
+// A row that lies entirely inside a chunk is written directly.  A row cut
+// by chunk boundaries leaves one partial per chunk it touches -- the tail of
+// the chunk it starts in, and the head of every later chunk -- and a fix-up
+// pass adds them in chunk order.  Rows without entries are zeroed first.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -15,27 +20,81 @@ namespace nmfg {
 namespace {
 
 constexpr int kWarps = 8;
+constexpr int64_t kChunk = 256;
+
+__device__ __forceinline__ int64_t row_of(const int64_t *__restrict__ ptr, int64_t rows,
+                                          int64_t q) {
+    // Largest row with ptr[row] <= q (q < nnz).
+    int64_t lo = 0, hi = rows - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (ptr[mid] <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 template <int E>
+__device__ __forceinline__ void store_vec(float *dst, int64_t col_stride, const float (&acc)[E],
+                                          int lane, int r) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = lane + 32 * e;
+        if (k < r) dst[(int64_t)k * col_stride] = acc[e];
+    }
+}
+
+// out[row * ors + k * ocs] = sum_{q in row} val[q] * F[idx[q] * rs + k].
+// head[c] / tail[c] (rs floats each) receive the partials of rows cut by the
+// chunk boundaries.
+template <int E>
 __global__ void __launch_bounds__(kWarps * 32)
-spmm_rows_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                 const float *__restrict__ val, int64_t rows, int r, int rs,
-                 const float *__restrict__ F,           // gathered factor, (cols) x rs
-                 float *__restrict__ out, int64_t out_row_stride, int64_t out_col_stride) {
+spmm_chunks_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                   const float *__restrict__ val, int64_t rows, int64_t nnz, int r, int rs,
+                   const float *__restrict__ F, float *__restrict__ out, int64_t ors,
+                   int64_t ocs, float *__restrict__ head, float *__restrict__ tail) {
     const int lane = threadIdx.x % 32;
-    const int64_t row = (int64_t)blockIdx.x * kWarps + threadIdx.x / 32;
-    if (row >= rows) return;
+    const int64_t c = (int64_t)blockIdx.x * kWarps + threadIdx.x / 32;
+    const int64_t q0 = c * kChunk;
+    if (q0 >= nnz) return;
+    const int64_t q1 = min(nnz, q0 + kChunk);
+    int64_t row = row_of(ptr, rows, q0);
+    int64_t row_end = ptr[row + 1];
+    bool started_before = ptr[row] < q0;
     float acc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[e] = 0.0f;
-    const int64_t p0 = ptr[row], p1 = ptr[row + 1];
-    for (int64_t base = p0; base < p1; base += 32) {
+
+    auto flush = [&](bool continues) {
+        float *dst;
+        int64_t stride = 1;
+        if (started_before) {
+            dst = head + c * rs;
+        } else if (continues) {
+            dst = tail + c * rs;
+        } else {
+            dst = out + row * ors;
+            stride = ocs;
+        }
+        store_vec<E>(dst, stride, acc, lane, r);
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.0f;
+    };
+
+    for (int64_t base = q0; base < q1; base += 32) {
         const int64_t q = base + lane;
-        const int32_t c = q < p1 ? idx[q] : 0;
-        const float v = q < p1 ? val[q] : 0.0f;
-        const int cnt = (p1 - base) < 32 ? (int)(p1 - base) : 32;
+        const int32_t cidx = q < q1 ? idx[q] : 0;
+        const float v = q < q1 ? val[q] : 0.0f;
+        const int cnt = (q1 - base) < 32 ? (int)(q1 - base) : 32;
         for (int u = 0; u < cnt; ++u) {
-            const int32_t cu = __shfl_sync(0xffffffffu, c, u);
+            const int64_t qu = base + u;
+            while (qu >= row_end) {          // next non-empty row
+                flush(false);
+                started_before = false;
+                ++row;
+                row_end = ptr[row + 1];
+            }
+            const int32_t cu = __shfl_sync(0xffffffffu, cidx, u);
             const float vu = __shfl_sync(0xffffffffu, v, u);
             const float *f = F + (int64_t)cu * rs;
 #pragma unroll
@@ -45,31 +104,64 @@ spmm_rows_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ id
             }
         }
     }
+    flush(row_end > q1);
+}
+
+// For every chunk whose last row starts inside it and continues past it:
+// tail[c] + head[c+1] + ... + head[c_end] in chunk order.
+template <int E>
+__global__ void __launch_bounds__(kWarps * 32)
+spmm_fixup_kernel(const int64_t *__restrict__ ptr, int64_t rows, int64_t nnz, int r, int rs,
+                  float *__restrict__ out, int64_t ors, int64_t ocs,
+                  const float *__restrict__ head, const float *__restrict__ tail) {
+    const int lane = threadIdx.x % 32;
+    const int64_t c = (int64_t)blockIdx.x * kWarps + threadIdx.x / 32;
+    const int64_t q0 = c * kChunk;
+    if (q0 >= nnz) return;
+    const int64_t q1 = min(nnz, q0 + kChunk);
+    const int64_t row = row_of(ptr, rows, q1 - 1);
+    if (ptr[row + 1] <= q1 || ptr[row] < q0) return;   // not a row that starts here and continues
+    const int64_t c_end = (ptr[row + 1] - 1) / kChunk;
+    float acc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int k = lane + 32 * e;
-        if (k < r) out[row * out_row_stride + (int64_t)k * out_col_stride] = acc[e];
-        else if (k < rs && out_col_stride == 1) out[row * out_row_stride + k] = 0.0f;
+        acc[e] = k < rs ? tail[c * rs + k] : 0.0f;
     }
+    for (int64_t cc = c + 1; cc <= c_end; ++cc) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = lane + 32 * e;
+            if (k < rs) acc[e] += head[cc * rs + k];
+        }
+    }
+    store_vec<E>(out + row * ors, ocs, acc, lane, r);
 }
 
 template <int E>
 cudaError_t spmm_launch(const int64_t *ptr, const int32_t *idx, const float *val, int64_t rows,
-                        int r, int rs, const float *F, float *out, int64_t ors, int64_t ocs,
-                        cudaStream_t st) {
-    const unsigned grid = (unsigned)((rows + kWarps - 1) / kWarps);
+                        int64_t nnz, int r, int rs, const float *F, float *out, int64_t ors,
+                        int64_t ocs, float *head, float *tail, cudaStream_t st) {
+    const int64_t chunks = (nnz + kChunk - 1) / kChunk;
+    const unsigned grid = (unsigned)((chunks + kWarps - 1) / kWarps);
     if (grid == 0) return cudaSuccess;
-    spmm_rows_kernel<E><<<grid, kWarps * 32, 0, st>>>(ptr, idx, val, rows, r, rs, F, out, ors, ocs);
+    spmm_chunks_kernel<E><<<grid, kWarps * 32, 0, st>>>(ptr, idx, val, rows, nnz, r, rs, F, out,
+                                                        ors, ocs, head, tail);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    spmm_fixup_kernel<E><<<grid, kWarps * 32, 0, st>>>(ptr, rows, nnz, r, rs, out, ors, ocs, head,
+                                                       tail);
     return cudaGetLastError();
 }
 
-cudaError_t spmm(const int64_t *ptr, const int32_t *idx, const float *val, int64_t rows, int r,
-                 int rs, const float *F, float *out, int64_t ors, int64_t ocs, cudaStream_t st) {
+cudaError_t spmm(const int64_t *ptr, const int32_t *idx, const float *val, int64_t rows,
+                 int64_t nnz, int r, int rs, const float *F, float *out, int64_t ors, int64_t ocs,
+                 float *head, float *tail, cudaStream_t st) {
     switch ((rs + 31) / 32) {
-        case 1: return spmm_launch<1>(ptr, idx, val, rows, r, rs, F, out, ors, ocs, st);
-        case 2: return spmm_launch<2>(ptr, idx, val, rows, r, rs, F, out, ors, ocs, st);
-        case 3: return spmm_launch<3>(ptr, idx, val, rows, r, rs, F, out, ors, ocs, st);
-        case 4: return spmm_launch<4>(ptr, idx, val, rows, r, rs, F, out, ors, ocs, st);
+        case 1: return spmm_launch<1>(ptr, idx, val, rows, nnz, r, rs, F, out, ors, ocs, head, tail, st);
+        case 2: return spmm_launch<2>(ptr, idx, val, rows, nnz, r, rs, F, out, ors, ocs, head, tail, st);
+        case 3: return spmm_launch<3>(ptr, idx, val, rows, nnz, r, rs, F, out, ors, ocs, head, tail, st);
+        case 4: return spmm_launch<4>(ptr, idx, val, rows, nnz, r, rs, F, out, ors, ocs, head, tail, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -95,15 +187,29 @@ __global__ void transpose_h_kernel(const float *__restrict__ H, int r, int64_t n
 
 }  // namespace
 
-cudaError_t launch_xht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
-                           int64_t m, int r, int rs, const float *Ht, float *C, cudaStream_t st) {
-    return spmm(rowptr, colidx, val, m, r, rs, Ht, C, rs, 1, st);
+size_t csr_carry_floats(int64_t nnz, int rs) {
+    const int64_t chunks = (nnz + kChunk - 1) / kChunk;
+    return (size_t)(chunks > 0 ? chunks : 1) * rs * 2;
 }
 
+// C (m x rs) = X H^T; the whole of C is rewritten (rows without entries are 0).
+cudaError_t launch_xht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
+                           int64_t m, int64_t nnz, int r, int rs, const float *Ht, float *C,
+                           float *carry, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(C, 0, sizeof(float) * (size_t)m * rs, st);
+    if (e != cudaSuccess) return e;
+    const size_t half = csr_carry_floats(nnz, rs) / 2;
+    return spmm(rowptr, colidx, val, m, nnz, r, rs, Ht, C, rs, 1, carry, carry + half, st);
+}
+
+// A (r x lda) = W^T X from the CSC copy; columns without entries are 0.
 cudaError_t launch_wtx_csc(const int64_t *colptr, const int32_t *rowidx, const float *val,
-                           int64_t n, int r, int rs, const float *W, float *A, int64_t lda,
-                           cudaStream_t st) {
-    return spmm(colptr, rowidx, val, n, r, rs, W, A, 1, lda, st);
+                           int64_t n, int64_t nnz, int r, int rs, const float *W, float *A,
+                           int64_t lda, float *carry, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(A, 0, sizeof(float) * (size_t)r * lda, st);
+    if (e != cudaSuccess) return e;
+    const size_t half = csr_carry_floats(nnz, rs) / 2;
+    return spmm(colptr, rowidx, val, n, nnz, r, rs, W, A, 1, lda, carry, carry + half, st);
 }
 
 cudaError_t launch_transpose_h(const float *H, int r, int64_t n, int64_t ldh, float *Ht, int rs,

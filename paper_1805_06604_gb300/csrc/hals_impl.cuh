@@ -70,7 +70,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // Algorithm 3 and steps 16-20 of Algorithm 2, run by one thread.
 __device__ void decide_and_update_beta(DevState *s, const DevParams &p, const DevTrace &t,
                                        double cross, double quad) {
-    const double e2 = s->fro2 - 2.0 * cross + quad;                 // Remark 1
+    // Remark 1 in residual form: ||X||^2 - <W_n, C> + <W_n, W_n D - C>.
+    const double e2 = s->fro2 - cross + quad;
     const double e = sqrt(e2 > 0.0 ? e2 : 0.0);
     const int finite = isfinite(e2) ? 1 : 0;
     if (!finite) s->status = (int)NMF_ENONFINITE;
@@ -106,37 +107,47 @@ __device__ void decide_and_update_beta(DevState *s, const DevParams &p, const De
 // G(kk, j) x_j over its coordinates j = s*T + t outside E_kk.  With D = T,
 // E_kk \ {kk} = {g, ..., g+T-1} (g = kk - T mod RP) holds exactly one
 // coordinate of every lane, in slot g/T (lanes t >= g%T) or slot g/T + 1
-// (lanes t < g%T); kk itself sits in slot g/T + 1 of lane g%T.
-template <int T, int S, int SP, int KK>
-__device__ __forceinline__ float partial_dot(const float *Grow, int t, const float (&x)[S],
+// (lanes t < g%T); kk itself sits in slot g/T + 1 of lane g%T.  `gv` is the
+// lane's slice of Gram row kk (prefetched).  The slot of coordinate g-1,
+// written by the update just before, is accumulated last.
+template <int T, int S, int KK>
+__device__ __forceinline__ float partial_dot(const float (&gv)[S], int t, const float (&x)[S],
                                              const float (&a)[S]) {
     constexpr int RP = S * T;
     constexpr int G0 = (KK - T + RP) % RP;
     constexpr int SA = G0 / T;                 // first candidate slot
     constexpr int SB = (SA + 1) % S;           // second candidate slot
     constexpr int GR = G0 % T;
-    const float *row = Grow + KK * (T * SP) + t * SP;
-    // Two accumulators halve the dependent FMA chain.
-    float p0 = (t == KK % T) ? a[KK / T] : 0.0f, p1 = 0.0f;
-#pragma unroll
-    for (int q = 0; q < SP / 4; ++q) {
-        const float4 v = lds4(row + 4 * q);
-        const float gv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int s = 4 * q + u;
-            if (s >= S) continue;
-            float &p = (s & 1) ? p1 : p0;
-            if (s == SA) {
-                if (t < GR) p = fmaf(-gv[u], x[s], p);      // slot SA excluded for t >= GR
-            } else if (s == SB) {
-                if (t > GR) p = fmaf(-gv[u], x[s], p);      // slot SB excluded for t <= GR
-            } else {
-                p = fmaf(-gv[u], x[s], p);
-            }
+    constexpr int SL = ((G0 - 1 + RP) % RP) / T;   // slot of the newest coordinate
+    float p[4] = {(t == KK % T) ? a[KK / T] : 0.0f, 0.0f, 0.0f, 0.0f};
+    auto term = [&](int s) {
+        float &acc = p[s & 3];
+        if (s == SA) {
+            if (t < GR) acc = fmaf(-gv[s], x[s], acc);      // slot SA excluded for t >= GR
+        } else if (s == SB) {
+            if (t > GR) acc = fmaf(-gv[s], x[s], acc);      // slot SB excluded for t <= GR
+        } else {
+            acc = fmaf(-gv[s], x[s], acc);
         }
+    };
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+        if (s != SL) term(s);
+    term(SL);
+    return (p[0] + p[1]) + (p[2] + p[3]);
+}
+
+// Lane t's slice of Gram row k (S values, 16-byte aligned, SP >= S).
+template <int S, int SP>
+__device__ __forceinline__ void load_slice(float (&gv)[S], const float *row) {
+#pragma unroll
+    for (int q = 0; q < (S + 3) / 4; ++q) {
+        const float4 v = lds4(row + 4 * q);
+        if (4 * q + 0 < S) gv[4 * q + 0] = v.x;
+        if (4 * q + 1 < S) gv[4 * q + 1] = v.y;
+        if (4 * q + 2 < S) gv[4 * q + 2] = v.z;
+        if (4 * q + 3 < S) gv[4 * q + 3] = v.w;
     }
-    return p0 + p1;
 }
 
 template <int T>
@@ -156,20 +167,32 @@ hals_kernel(int64_t items, int r, int64_t ld,
             int hoist_guard, HEpilogue hep, WEpilogue wep) {
     constexpr int RP = S * T;                    // padded item length
     constexpr int D = T;                         // lookahead depth
-    constexpr int SP = 4 * ((S + 3) / 4);        // per-lane slice, 16-byte aligned
+    // Per-lane slice stride: 16-byte aligned and an odd number of 16-byte
+    // units, so the T slices a warp reads in one phase fall in distinct banks.
+    constexpr int SP = 4 * ((S + 3) / 4) + (((S + 3) / 4) % 2 == 0 ? 4 : 0);
     constexpr int ROW = T * SP;                  // one permuted Gram row
     static_assert(S >= 2, "the lookahead needs RP >= 2T");
     extern __shared__ __align__(16) float smem[];
     float *Grow = smem;                          // [RP][T][SP]: Grow[k][t][s] = G(k, s*T+t)
     float *Band = smem + RP * ROW;               // [RP][8]: G(k,k-1..k-D), 1/G(k,k)
+    float *Glo = Band + RP * 8;                  // W side with error terms: low part of D
     __shared__ double red_cross[kThreads / 32], red_quad[kThreads / 32];
     __shared__ bool am_last;
+    const bool err_terms = LAYOUT == kRow && wep.partials != nullptr;
 
     for (int idx = threadIdx.x; idx < RP * ROW; idx += blockDim.x) {
         const int k = idx / ROW, rem = idx % ROW;
         const int tt = rem / SP, s = rem % SP;
         const int i = s * T + tt;
         Grow[idx] = (k < r && s < S && i < r) ? Gglob[k * rs + i] : 0.0f;
+    }
+    if (err_terms) {
+        for (int idx = threadIdx.x; idx < RP * ROW; idx += blockDim.x) {
+            const int k = idx / ROW, rem = idx % ROW;
+            const int tt = rem / SP, s = rem % SP;
+            const int i = s * T + tt;
+            Glo[idx] = (k < r && s < S && i < r) ? wep.D_lo[k * rs + i] : 0.0f;
+        }
     }
     for (int idx = threadIdx.x; idx < RP * 8; idx += blockDim.x) {
         const int k = idx / 8, c = idx % 8;
@@ -201,19 +224,45 @@ hals_kernel(int64_t items, int r, int64_t ld,
         a[s] = in ? Aglob[elem_index<LAYOUT>(item, k, ld)] : 0.0f;
     }
 
-    // Pipeline state: P[k % D] = P_k for the next D updates, hist[k % D] =
-    // the newest values x_{k-1..k-D} (replicated in the group).
-    float P[D], hist[D];
+    // Pipeline state.  hist[k % D]: the newest values x_{k-1..k-D}
+    // (replicated in the group).  P[k % D]: reduced P_k.  The butterfly that
+    // combines the T lane shares of a partial is spread over consecutive
+    // updates -- stage i of the partial computed i updates earlier -- so no
+    // shuffle result is consumed in the update that issued it:
+    //   stage[0] = raw share of P_{k+D-1}, stage[1] = P_{k+D-2} after one
+    //   exchange (T = 4 only).  The Gram slice of the next partial and the
+    //   band of the next update are prefetched one update ahead.
+    constexpr int NST = (T == 4) ? 2 : 1;     // butterfly stages = log2(T)
+    float P[D], hist[D], stage[NST];
 #pragma unroll
     for (int d = 1; d <= D; ++d) {
         const int j = RP - d;                       // "previous sweep" coordinates
         hist[j % D] = __shfl_sync(gmask, x[j / T], j % T, T);
     }
-    // Prologue: P_0 .. P_{D-1} from the initial iterate.
-#define NMF_PROLOGUE(KK) \
-    if (KK < D) P[KK % D] = group_allreduce<T>(partial_dot<T, S, SP, KK % RP>(Grow, t, x, a));
-    NMF_PROLOGUE(0) NMF_PROLOGUE(1) NMF_PROLOGUE(2) NMF_PROLOGUE(3)
-#undef NMF_PROLOGUE
+    float gv[S];
+    // Prologue: complete P_0 .. P_{D-NST-1}; P_{D-NST} .. P_{D-1} enter the
+    // butterfly pipeline at the stage they would have reached.
+    [&]<int... J>(std::integer_sequence<int, J...>) {
+        (
+            [&] {
+                constexpr int kk = J;
+                load_slice<S, SP>(gv, Grow + kk * ROW + t * SP);
+                const float v = partial_dot<T, S, kk>(gv, t, x, a);
+                if constexpr (kk < D - NST) {
+                    P[kk % D] = group_allreduce<T>(v);        // complete
+                } else if constexpr (kk == D - 1) {
+                    stage[0] = v;                             // raw share of P_{D-1}
+                } else {
+                    stage[1] = v + __shfl_xor_sync(gmask, v, 1, T);   // P_{D-2}, one exchange
+                }
+            }(),
+            ...);
+    }(std::make_integer_sequence<int, D>{});
+    // Band values are read as warp-wide broadcast scalars (one wavefront each).
+    float bnext[D + 1];
+#pragma unroll
+    for (int d = 0; d <= D; ++d) bnext[d] = Band[d];
+    load_slice<S, SP>(gv, Grow + (D % RP) * ROW + t * SP);
 
 #pragma unroll 1
     for (int l = 0; l < sweeps; ++l) {
@@ -224,22 +273,40 @@ hals_kernel(int64_t items, int r, int64_t ld,
             (
                 [&] {
                     constexpr int k = K;
+                    constexpr int kk = (k + D) % RP;          // partial computed now
+                    // Prefetch the band of update k+1 and the Gram slice of
+                    // the partial of update k+1+D.
+                    float bcur[D + 1];
+#pragma unroll
+                    for (int d = 0; d <= D; ++d) bcur[d] = bnext[d];
+                    {
+                        const float *band = Bl + ((k + 1) % RP) * 8;
+#pragma unroll
+                        for (int d = 0; d <= D; ++d) bnext[d] = band[d];
+                    }
+                    float gcur[S];
+#pragma unroll
+                    for (int s2 = 0; s2 < S; ++s2) gcur[s2] = gv[s2];
+                    load_slice<S, SP>(gv, Gl + ((kk + 1) % RP) * ROW + t * SP);
+                    // Butterfly stages of earlier partials (results used later).
+                    if constexpr (NST == 2) {
+                        const float done = stage[1] + __shfl_xor_sync(gmask, stage[1], 2, T);
+                        stage[1] = stage[0] + __shfl_xor_sync(gmask, stage[0], 1, T);
+                        P[(k + D - 2) % D] = done;
+                    } else {
+                        P[(k + D - 1) % D] = stage[0] + __shfl_xor_sync(gmask, stage[0], 1, T);
+                    }
                     // Chain of update k.
-                    const float *band = Bl + k * 8;
-                    const float4 b0 = lds4(band);
-                    const float4 b1 = lds4(band + 4);
-                    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                     float s_k = P[k % D];
 #pragma unroll
                     for (int d = D; d >= 1; --d)
-                        s_k = fmaf(-bv[d - 1], hist[(k - d + RP) % D], s_k);
-                    const float inv = bv[D];
+                        s_k = fmaf(-bcur[d - 1], hist[(k - d + RP) % D], s_k);
+                    const float inv = bcur[D];
                     const float h = fmaxf(s_k * inv, 0.0f);
                     if (t == k % T && inv > 0.0f) x[k / T] = h;
                     hist[k % D] = h;
-                    // Partial dots of update k + D (coordinates final before k).
-                    constexpr int kk = (k + D) % RP;
-                    P[kk % D] = group_allreduce<T>(partial_dot<T, S, SP, kk>(Gl, t, x, a));
+                    // Raw share of the partial of update k + D.
+                    stage[0] = partial_dot<T, S, kk>(gcur, t, x, a);
                 }(),
                 ...);
         }(std::make_integer_sequence<int, RP>{});
@@ -270,31 +337,42 @@ hals_kernel(int64_t items, int r, int64_t ld,
         }
     }
 
-    if (LAYOUT == kRow && wep.partials != nullptr) {
-        // Remark 1 terms of this row: <w, c> and w . (D w), D w recomputed
-        // from the final w.
-        float dw[S];
+    if (err_terms) {
+        // Remark 1 for this row, in the residual form
+        //   ||x - w H||^2 contribution = -<w, c> + <w, R>,  R = D w - c,
+        // which equals -2<w, c> + w.(D w) exactly.  Near convergence R is
+        // small, so only <w, c> cancels against ||X||^2: it is summed in
+        // FP64 from c = C + C_lo, and R is evaluated with error-free
+        // products and sums from D + D_lo (both accurate to about 2^-40).
+        float hi[S], lo[S], clo[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) dw[s] = 0.0f;
-#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int k = s * T + t;
+            clo[s] = (valid && k < r) ? wep.C_lo[elem_index<LAYOUT>(item, k, ld)] : 0.0f;
+            hi[s] = -a[s];
+            lo[s] = -clo[s];
+        }
+#pragma unroll 1
         for (int j = 0; j < RP; ++j) {
             const float wj = __shfl_sync(gmask, x[j / T], j % T, T);
-            const float *row = Grow + j * ROW + t * SP;      // D(j, s*T+t) = D(s*T+t, j)
+            const float *row_hi = Grow + j * ROW + t * SP;   // D(j, s*T+t) = D(s*T+t, j)
+            const float *row_lo = Glo + j * ROW + t * SP;
 #pragma unroll
-            for (int q = 0; q < SP / 4; ++q) {
-                const float4 v = lds4(row + 4 * q);
-                const float gv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (4 * q + u < S) dw[4 * q + u] = fmaf(gv[u], wj, dw[4 * q + u]);
+            for (int s = 0; s < S; ++s) {
+                const float dh = row_hi[s], dl = row_lo[s];
+                const float p = dh * wj;
+                const float pe = fmaf(dh, wj, -p);
+                const float sum = hi[s] + p, bb = sum - hi[s];
+                lo[s] += ((hi[s] - (sum - bb)) + (p - bb)) + pe + dl * wj;
+                hi[s] = sum;
             }
         }
         double cross = 0.0, quad = 0.0;
         if (valid) {
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                cross = fma((double)x[s], (double)a[s], cross);
-                quad = fma((double)x[s], (double)dw[s], quad);
+                cross = fma((double)x[s], (double)a[s] + (double)clo[s], cross);
+                quad = fma((double)x[s], (double)hi[s] + (double)lo[s], quad);
             }
         }
         cross = warp_sum_d(cross);
@@ -357,8 +435,8 @@ cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const 
                         const float *Xin, float *Xout, int sweeps, const HEpilogue &hep,
                         const WEpilogue &wep, cudaStream_t st) {
     constexpr int RP = S * T;
-    constexpr int SP = 4 * ((S + 3) / 4);
-    const size_t smem = sizeof(float) * (size_t)(RP * T * SP + RP * 8);
+    constexpr int SP = 4 * ((S + 3) / 4) + (((S + 3) / 4) % 2 == 0 ? 4 : 0);
+    const size_t smem = sizeof(float) * (size_t)(RP * T * SP * (LAYOUT == 1 ? 2 : 1) + RP * 8);
     auto kern = hals_kernel<T, S, LAYOUT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

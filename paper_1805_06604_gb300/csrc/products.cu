@@ -51,32 +51,38 @@ __device__ __forceinline__ void kahan_add(float &sum, float &c, float v) {
 template <int TM, int TR>
 __global__ void __launch_bounds__(kThreads)
 xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
-               const float *__restrict__ H, int64_t ldh, float *__restrict__ C, int rs) {
+               const float *__restrict__ H, int64_t ldh, float *__restrict__ C,
+               float *__restrict__ C_lo, int rs, int64_t cols_per_split,
+               float *__restrict__ part, unsigned int *__restrict__ tickets) {
     constexpr int BM = 16 * TM;
     constexpr int R = 8 * TR;
     extern __shared__ __align__(16) float sm[];
     float *Xs = sm;                                   // [kStages][BM][PADK]
     float *Hs = sm + kStages * BM * PADK;             // [kStages][R][PADK]
+    __shared__ bool am_last;
 
     const int tid = threadIdx.x;
     const int tx = tid % 8, ty = tid / 8;
     const int64_t row0 = (int64_t)blockIdx.x * BM;
-    const int64_t nk = (ldx + BK - 1) / BK;
+    const int split = blockIdx.y, nsplit = gridDim.y;
+    const int64_t kbeg = (int64_t)split * cols_per_split;
+    const int64_t kend = min(ldx, kbeg + cols_per_split);
+    const int64_t nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
 
     auto load_stage = [&](int stage, int64_t kt) {
-        const int64_t k0 = kt * BK;
+        const int64_t k0 = kbeg + kt * BK;
         float *xs = Xs + stage * BM * PADK;
         for (int idx = tid; idx < BM * (BK / 4); idx += kThreads) {
             const int rr = idx / (BK / 4), c4 = idx % (BK / 4);
             const int64_t grow = row0 + rr, gcol = k0 + c4 * 4;
-            const bool ok = grow < m && gcol < ldx;
+            const bool ok = grow < m && gcol < kend;
             cp_async16(xs + rr * PADK + c4 * 4, ok ? X + grow * ldx + gcol : X, ok);
         }
         float *hs = Hs + stage * R * PADK;
         for (int idx = tid; idx < R * (BK / 4); idx += kThreads) {
             const int kk = idx / (BK / 4), c4 = idx % (BK / 4);
             const int64_t gcol = k0 + c4 * 4;
-            const bool ok = kk < r && gcol < ldh;
+            const bool ok = kk < r && gcol < kend;
             cp_async16(hs + kk * PADK + c4 * 4, ok ? H + (int64_t)kk * ldh + gcol : H, ok);
         }
     };
@@ -135,33 +141,82 @@ xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     }
     cp_async_wait<0>();
 
+    // The compensated sum is acc - comp; C keeps its FP32 rounding and C_lo
+    // the remainder (the Remark 1 error term <W, C> uses both).
+    if (nsplit == 1) {
 #pragma unroll
-    for (int a = 0; a < TM; ++a) {
-        const int64_t row = row0 + ty + 16 * a;
-        if (row >= m) continue;
+        for (int a = 0; a < TM; ++a) {
+            const int64_t row = row0 + ty + 16 * a;
+            if (row >= m) continue;
+#pragma unroll
+            for (int b = 0; b < TR; ++b) {
+                const int col = tx + 8 * b;
+                if (col < rs) {
+                    const float hi = acc[a][b] - comp[a][b];
+                    C[row * rs + col] = hi;
+                    C_lo[row * rs + col] = (acc[a][b] - hi) - comp[a][b];
+                }
+            }
+        }
+        return;
+    }
+    // Split-K over the columns of X: partial tiles (hi, lo), summed in split
+    // order by the last split of the row tile to finish.
+    float *my = part + ((int64_t)blockIdx.x * nsplit + split) * (2 * BM * R);
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
 #pragma unroll
         for (int b = 0; b < TR; ++b) {
-            const int col = tx + 8 * b;
-            if (col < rs) C[row * rs + col] = acc[a][b] - comp[a][b];
+            const float hi = acc[a][b] - comp[a][b];
+            my[(ty + 16 * a) * R + tx + 8 * b] = hi;
+            my[BM * R + (ty + 16 * a) * R + tx + 8 * b] = (acc[a][b] - hi) - comp[a][b];
+        }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned int tk = atomicAdd(tickets + blockIdx.x, 1u);
+        am_last = (tk == (unsigned)nsplit - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    const float *base = part + (int64_t)blockIdx.x * nsplit * (2 * BM * R);
+    for (int e = tid; e < BM * R; e += kThreads) {
+        float hi = 0.0f, lo = 0.0f;
+        for (int q = 0; q < nsplit; ++q) {
+            const float v = __ldcg(base + (int64_t)q * 2 * BM * R + e);
+            const float s = hi + v, bb = s - hi;
+            lo += (hi - (s - bb)) + (v - bb) + __ldcg(base + (int64_t)q * 2 * BM * R + BM * R + e);
+            hi = s;
+        }
+        const int64_t row = row0 + e / R;
+        const int col = e % R;
+        if (row < m && col < rs) {
+            const float c = hi + lo;
+            C[row * rs + col] = c;
+            C_lo[row * rs + col] = (hi - c) + lo;
         }
     }
+    if (tid == 0) tickets[blockIdx.x] = 0u;
 }
 
 // ---------------------------------------------------------------------------
-// A = W^T X.  CTA: BN = 64 columns of X, all R = 8*TR rows of A, rows
-// [i_begin, i_end) of X.  Thread (tx in 0..15, ty in 0..7) owns columns
-// 4tx..4tx+3 and rows ty + 8b of A.
+// A = W^T X.  CTA: BN = 128 columns of X, all R = rs rows of A, rows
+// [i_begin, i_end) of X (a split of the reduction).  4R threads: thread
+// (g, tx), g < R/4, tx < 16, owns the rows 4g..4g+3 of A and the columns
+// 4tx..4tx+3 and 64+4tx..64+4tx+3 of the tile, so each X row of the stage
+// costs it three 16-byte shared loads for 32 FMAs.
 // ---------------------------------------------------------------------------
-constexpr int BN = 64;
+constexpr int BN = 128;
 constexpr int PADN = BN + 4;
 
-template <int TR>
-__global__ void __launch_bounds__(kThreads)
+template <int R>
+__global__ void __launch_bounds__(4 * R)
 wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
-               const float *__restrict__ W, int rs, float *__restrict__ A, int64_t lda,
+               const float *__restrict__ W, float *__restrict__ A, int64_t lda,
                int64_t rows_per_split, float *__restrict__ part,
                unsigned int *__restrict__ tickets) {
-    constexpr int R = 8 * TR;
+    constexpr int NT = 4 * R;
     constexpr int PADR = R + 4;
     extern __shared__ __align__(16) float sm[];
     float *Xs = sm;                                   // [kStages][BK][PADN]
@@ -169,7 +224,7 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     __shared__ bool am_last;
 
     const int tid = threadIdx.x;
-    const int tx = tid % 16, ty = tid / 16;
+    const int tx = tid % 16, g = tid / 16;
     const int64_t col0 = (int64_t)blockIdx.x * BN;
     const int split = blockIdx.y, nsplit = gridDim.y;
     const int64_t i_begin = (int64_t)split * rows_per_split;
@@ -179,26 +234,27 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     auto load_stage = [&](int stage, int64_t kt) {
         const int64_t i0 = i_begin + kt * BK;
         float *xs = Xs + stage * BK * PADN;
-        for (int idx = tid; idx < BK * (BN / 4); idx += kThreads) {
+        for (int idx = tid; idx < BK * (BN / 4); idx += NT) {
             const int ii = idx / (BN / 4), c4 = idx % (BN / 4);
             const int64_t grow = i0 + ii, gcol = col0 + c4 * 4;
             const bool ok = grow < i_end && gcol < ldx;
             cp_async16(xs + ii * PADN + c4 * 4, ok ? X + grow * ldx + gcol : X, ok);
         }
         float *ws = Ws + stage * BK * PADR;
-        for (int idx = tid; idx < BK * (R / 4); idx += kThreads) {
+        for (int idx = tid; idx < BK * (R / 4); idx += NT) {
             const int ii = idx / (R / 4), c4 = idx % (R / 4);
             const int64_t grow = i0 + ii;
-            const bool ok = grow < i_end && c4 * 4 < rs;
-            cp_async16(ws + ii * PADR + c4 * 4, ok ? W + grow * rs + c4 * 4 : W, ok);
+            const bool ok = grow < i_end;
+            cp_async16(ws + ii * PADR + c4 * 4, ok ? W + grow * R + c4 * 4 : W, ok);
         }
     };
 
-    float acc[TR][4], comp[TR][4];
+    // Compensated accumulation (see the file header).
+    float acc[4][8], comp[4][8];
 #pragma unroll
-    for (int b = 0; b < TR; ++b)
+    for (int b = 0; b < 4; ++b)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[b][c] = comp[b][c] = 0.0f;
+        for (int c = 0; c < 8; ++c) acc[b][c] = comp[b][c] = 0.0f;
 
 #pragma unroll
     for (int s = 0; s < kStages - 1; ++s) {
@@ -214,43 +270,45 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
 
         const float *xs = Xs + (kt % kStages) * BK * PADN;
         const float *ws = Ws + (kt % kStages) * BK * PADR;
-        float blk[TR][4];
+        float blk[4][8];
 #pragma unroll
-        for (int b = 0; b < TR; ++b)
+        for (int b = 0; b < 4; ++b)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) blk[b][c] = 0.0f;
-#pragma unroll 8
+            for (int c = 0; c < 8; ++c) blk[b][c] = 0.0f;
+#pragma unroll 4
         for (int ii = 0; ii < BK; ++ii) {
-            const float4 xv = *reinterpret_cast<const float4 *>(xs + ii * PADN + tx * 4);
+            const float4 w = *reinterpret_cast<const float4 *>(ws + ii * PADR + 4 * g);
+            const float4 x0 = *reinterpret_cast<const float4 *>(xs + ii * PADN + 4 * tx);
+            const float4 x1 = *reinterpret_cast<const float4 *>(xs + ii * PADN + 64 + 4 * tx);
+            const float wv[4] = {w.x, w.y, w.z, w.w};
+            const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-            for (int b = 0; b < TR; ++b) {
-                const float w = ws[ii * PADR + ty + 8 * b];
-                blk[b][0] = fmaf(w, xv.x, blk[b][0]);
-                blk[b][1] = fmaf(w, xv.y, blk[b][1]);
-                blk[b][2] = fmaf(w, xv.z, blk[b][2]);
-                blk[b][3] = fmaf(w, xv.w, blk[b][3]);
-            }
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) blk[b][c] = fmaf(wv[b], xv[c], blk[b][c]);
         }
 #pragma unroll
-        for (int b = 0; b < TR; ++b)
+        for (int b = 0; b < 4; ++b)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) kahan_add(acc[b][c], comp[b][c], blk[b][c]);
+            for (int c = 0; c < 8; ++c) kahan_add(acc[b][c], comp[b][c], blk[b][c]);
     }
     cp_async_wait<0>();
 #pragma unroll
-    for (int b = 0; b < TR; ++b)
+    for (int b = 0; b < 4; ++b)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[b][c] -= comp[b][c];
+        for (int c = 0; c < 8; ++c) acc[b][c] -= comp[b][c];
 
+    auto col_of = [&](int c) -> int64_t { return col0 + (c < 4 ? 4 * tx + c : 64 + 4 * tx + c - 4); };
     if (nsplit == 1) {
 #pragma unroll
-        for (int b = 0; b < TR; ++b) {
-            const int k = ty + 8 * b;
+        for (int b = 0; b < 4; ++b) {
+            const int k = 4 * g + b;
             if (k >= r) continue;
-            const int64_t j = col0 + tx * 4;
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (j + c < lda) A[(int64_t)k * lda + j + c] = acc[b][c];
+            for (int c = 0; c < 8; ++c) {
+                const int64_t j = col_of(c);
+                if (j < lda) A[(int64_t)k * lda + j] = acc[b][c];
+            }
         }
         return;
     }
@@ -259,9 +317,13 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     // column tile sums the partials in split order.
     float *my = part + ((int64_t)blockIdx.x * nsplit + split) * (R * BN);
 #pragma unroll
-    for (int b = 0; b < TR; ++b)
-        *reinterpret_cast<float4 *>(my + (ty + 8 * b) * BN + tx * 4) =
+    for (int b = 0; b < 4; ++b) {
+        float *rowp = my + (4 * g + b) * BN;
+        *reinterpret_cast<float4 *>(rowp + 4 * tx) =
             make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+        *reinterpret_cast<float4 *>(rowp + 64 + 4 * tx) =
+            make_float4(acc[b][4], acc[b][5], acc[b][6], acc[b][7]);
+    }
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -272,7 +334,7 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     if (!am_last) return;
     __threadfence();
     const float *base = part + (int64_t)blockIdx.x * nsplit * (R * BN);
-    for (int e = tid * 4; e < R * BN; e += kThreads * 4) {
+    for (int e = tid * 4; e < R * BN; e += NT * 4) {
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f), c = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int q = 0; q < nsplit; ++q) {
             const float4 v = __ldcg(reinterpret_cast<const float4 *>(base + (int64_t)q * R * BN + e));
@@ -281,41 +343,36 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
             kahan_add(s.z, c.z, v.z);
             kahan_add(s.w, c.w, v.w);
         }
-        s.x -= c.x;
-        s.y -= c.y;
-        s.z -= c.z;
-        s.w -= c.w;
         const int k = e / BN;
         const int64_t j = col0 + e % BN;
         if (k < r) {
-            const float vv[4] = {s.x, s.y, s.z, s.w};
+            const float vv[4] = {s.x - c.x, s.y - c.y, s.z - c.z, s.w - c.w};
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (j + c < lda) A[(int64_t)k * lda + j + c] = vv[c];
+            for (int q = 0; q < 4; ++q)
+                if (j + q < lda) A[(int64_t)k * lda + j + q] = vv[q];
         }
     }
     if (tid == 0) tickets[blockIdx.x] = 0u;
 }
 
-template <int TR>
-cudaError_t wtx_launch(const float *X, int64_t m, int64_t ldx, int r, const float *W, int rs,
-                       float *A, int64_t lda, int nsplit, int64_t rows_per_split, float *part,
+template <int R>
+cudaError_t wtx_launch(const float *X, int64_t m, int64_t ldx, int r, const float *W, float *A,
+                       int64_t lda, int nsplit, int64_t rows_per_split, float *part,
                        unsigned int *tickets, cudaStream_t st) {
-    constexpr int R = 8 * TR;
     const size_t smem = sizeof(float) * (size_t)kStages * BK * (PADN + R + 4);
-    auto kern = wtx_f32_kernel<TR>;
+    auto kern = wtx_f32_kernel<R>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((lda + BN - 1) / BN), (unsigned)nsplit);
-    kern<<<grid, kThreads, smem, st>>>(X, m, ldx, r, W, rs, A, lda, rows_per_split, part,
-                                       tickets);
+    kern<<<grid, 4 * R, smem, st>>>(X, m, ldx, r, W, A, lda, rows_per_split, part, tickets);
     return cudaGetLastError();
 }
 
 template <int TM, int TR>
 cudaError_t xht_launch(const float *X, int64_t m, int64_t ldx, int r, const float *H,
-                       int64_t ldh, float *C, int rs, cudaStream_t st) {
+                       int64_t ldh, float *C, float *C_lo, int rs, int nsplit, float *part,
+                       unsigned int *tickets, cudaStream_t st) {
     constexpr int BM = 16 * TM;
     constexpr int R = 8 * TR;
     const size_t smem = sizeof(float) * (size_t)kStages * (BM + R) * PADK;
@@ -323,9 +380,33 @@ cudaError_t xht_launch(const float *X, int64_t m, int64_t ldx, int r, const floa
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)((m + BM - 1) / BM);
-    kern<<<grid, kThreads, smem, st>>>(X, m, ldx, r, H, ldh, C, rs);
+    const int64_t cols = ((ldx + nsplit - 1) / nsplit + BK - 1) / BK * BK;
+    dim3 grid((unsigned)((m + BM - 1) / BM), (unsigned)nsplit);
+    kern<<<grid, kThreads, smem, st>>>(X, m, ldx, r, H, ldh, C, C_lo, rs, cols, part, tickets);
     return cudaGetLastError();
+}
+
+// Row-tile height and column splits of C = X H^T: 64-row tiles once they
+// cover every SM (32-row tiles for r > 72, where the 64-row tile spills), and
+// enough splits of n for about two CTAs per SM.
+struct XhtPlan {
+    bool big;
+    int nsplit;
+    int64_t tiles;
+};
+
+XhtPlan plan_xht(int64_t m, int64_t ldx, int r) {
+    XhtPlan p;
+    p.big = m >= (int64_t)kNumSMs * 64 && r <= 72;
+    const int64_t bm = p.big ? 64 : 32;
+    p.tiles = (m + bm - 1) / bm;
+    int64_t want = (2 * kNumSMs + p.tiles - 1) / p.tiles;
+    const int64_t max_split = (ldx + 8 * BK - 1) / (8 * BK);   // >= 256 columns per split
+    if (want > max_split) want = max_split;
+    if (want < 1) want = 1;
+    if (want > 16) want = 16;
+    p.nsplit = (int)want;
+    return p;
 }
 
 struct WtxPlan {
@@ -337,7 +418,7 @@ struct WtxPlan {
 WtxPlan plan_wtx(int64_t m, int64_t lda) {
     WtxPlan p;
     p.tiles = (lda + BN - 1) / BN;
-    int64_t want = (3 * kNumSMs + p.tiles - 1) / p.tiles;     // ~3 CTAs per SM
+    int64_t want = (2 * kNumSMs + p.tiles - 1) / p.tiles;     // ~2 CTAs per SM
     int64_t max_split = (m + 8 * BK - 1) / (8 * BK);         // >= 256 rows per split
     if (want > max_split) want = max_split;
     if (want < 1) want = 1;
@@ -364,29 +445,41 @@ cudaError_t launch_wtx_f32(const float *X, int64_t m, int64_t lda, int64_t ldx, 
                            cudaStream_t st) {
     const WtxPlan p = plan_wtx(m, lda);
     float *part = static_cast<float *>(ws);
-    switch ((r + 7) / 8) {
-#define NMF_WTX_CASE(TRV)                                                                     \
-    case TRV:                                                                                 \
-        return wtx_launch<TRV>(X, m, ldx, r, W, rs, A, lda, p.nsplit, p.rows_per_split, part, \
-                               tickets, st);
-        NMF_WTX_CASE(1) NMF_WTX_CASE(2) NMF_WTX_CASE(3) NMF_WTX_CASE(4)
-        NMF_WTX_CASE(5) NMF_WTX_CASE(6) NMF_WTX_CASE(7) NMF_WTX_CASE(8)
-        NMF_WTX_CASE(9) NMF_WTX_CASE(10) NMF_WTX_CASE(11) NMF_WTX_CASE(12)
-        NMF_WTX_CASE(13) NMF_WTX_CASE(14) NMF_WTX_CASE(15) NMF_WTX_CASE(16)
+    switch (rs) {
+#define NMF_WTX_CASE(RV)                                                                      \
+    case RV:                                                                                  \
+        return wtx_launch<RV>(X, m, ldx, r, W, A, lda, p.nsplit, p.rows_per_split, part,      \
+                              tickets, st);
+        NMF_WTX_CASE(8) NMF_WTX_CASE(16) NMF_WTX_CASE(24) NMF_WTX_CASE(32)
+        NMF_WTX_CASE(40) NMF_WTX_CASE(48) NMF_WTX_CASE(56) NMF_WTX_CASE(64)
+        NMF_WTX_CASE(72) NMF_WTX_CASE(80) NMF_WTX_CASE(88) NMF_WTX_CASE(96)
+        NMF_WTX_CASE(104) NMF_WTX_CASE(112) NMF_WTX_CASE(120) NMF_WTX_CASE(128)
 #undef NMF_WTX_CASE
         default: return cudaErrorInvalidValue;
     }
 }
 
+size_t xht_ws_bytes(int64_t m, int64_t ldx, int r) {
+    const XhtPlan p = plan_xht(m, ldx, r);
+    if (p.nsplit == 1) return 256;
+    const int64_t bm = p.big ? 64 : 32;
+    return 2 * sizeof(float) * (size_t)p.tiles * p.nsplit * bm * (8 * ((r + 7) / 8));
+}
+
+int64_t xht_num_tickets(int64_t m) { return (m + 31) / 32; }
+
 cudaError_t launch_xht_f32(const float *X, int64_t m, int64_t ldx, int r, const float *H,
-                           int64_t ldh, float *C, int rs, cudaStream_t st) {
-    // Two CTAs per SM worth of row tiles when m allows it; else 32-row tiles.
-    const bool big = m >= 2LL * kNumSMs * 64;
+                           int64_t ldh, float *C, float *C_lo, int rs, void *ws,
+                           unsigned int *tickets, cudaStream_t st) {
+    const XhtPlan p = plan_xht(m, ldx, r);
+    float *part = static_cast<float *>(ws);
     switch ((r + 7) / 8) {
-#define NMF_XHT_CASE(TRV)                                                           \
-    case TRV:                                                                       \
-        return big ? xht_launch<4, TRV>(X, m, ldx, r, H, ldh, C, rs, st)            \
-                   : xht_launch<2, TRV>(X, m, ldx, r, H, ldh, C, rs, st);
+#define NMF_XHT_CASE(TRV)                                                                      \
+    case TRV:                                                                                  \
+        return p.big ? xht_launch<4, TRV>(X, m, ldx, r, H, ldh, C, C_lo, rs, p.nsplit, part,     \
+                                          tickets, st)                                         \
+                     : xht_launch<2, TRV>(X, m, ldx, r, H, ldh, C, C_lo, rs, p.nsplit, part,     \
+                                          tickets, st);
         NMF_XHT_CASE(1) NMF_XHT_CASE(2) NMF_XHT_CASE(3) NMF_XHT_CASE(4)
         NMF_XHT_CASE(5) NMF_XHT_CASE(6) NMF_XHT_CASE(7) NMF_XHT_CASE(8)
         NMF_XHT_CASE(9) NMF_XHT_CASE(10) NMF_XHT_CASE(11) NMF_XHT_CASE(12)

@@ -43,6 +43,17 @@ __device__ __forceinline__ void kahan_add(float &sum, float &c, float v) {
     sum = t;
 }
 
+// Error-free transformations: a*b = p + e exactly (FMA), a+b = s + e exactly.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 2 * kNumSMs;
 
@@ -79,16 +90,20 @@ __global__ void sum_partials_kernel(const double *__restrict__ part, int count,
 // ROWS = false: M is r x ldm (entries M[k*ldm + i], i < N), G = M M^T.
 constexpr int GBK = 32;
 
-template <int RB, bool ROWS>
+// EXACT = false: 32-row blocks summed in FP32, blocks combined with Kahan's
+// correction (the Gram feeds the sweeps; FP32 accuracy).  EXACT = true: every
+// product and sum goes through an error-free transformation and the result
+// is kept as an unevaluated pair hi + lo (the Gram of H_y also feeds the
+// Remark 1 error, whose cancellation needs it to about 2^-40 relative).
+template <int RB, bool ROWS, bool EXACT>
 __global__ void __launch_bounds__(256)
 gram_partial_kernel(const float *__restrict__ M, int64_t N, int64_t ldm, int r,
-                    int64_t chunk, float *__restrict__ part, int rs) {
+                    int64_t chunk, float *__restrict__ part, float *__restrict__ part_lo, int rs) {
     constexpr int R = 16 * RB;
     __shared__ float Ms[GBK][R + 1];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int64_t i0 = (int64_t)blockIdx.x * chunk;
     const int64_t i1 = min(N, i0 + chunk);
-    // 32-row blocks summed in FP32, blocks combined with Kahan's correction.
     float acc[RB][RB], comp[RB][RB];
 #pragma unroll
     for (int a = 0; a < RB; ++a)
@@ -111,27 +126,48 @@ gram_partial_kernel(const float *__restrict__ M, int64_t N, int64_t ldm, int r,
             Ms[ii][k] = v;
         }
         __syncthreads();
-        float blk[RB][RB];
+        if constexpr (EXACT) {
+#pragma unroll 2
+            for (int ii = 0; ii < GBK; ++ii) {
+                float va[RB], vb[RB];
 #pragma unroll
-        for (int a = 0; a < RB; ++a)
+                for (int a = 0; a < RB; ++a) va[a] = Ms[ii][ty + 16 * a];
 #pragma unroll
-            for (int b = 0; b < RB; ++b) blk[a][b] = 0.0f;
-#pragma unroll 4
-        for (int ii = 0; ii < GBK; ++ii) {
-            float va[RB], vb[RB];
+                for (int b = 0; b < RB; ++b) vb[b] = Ms[ii][tx + 16 * b];
 #pragma unroll
-            for (int a = 0; a < RB; ++a) va[a] = Ms[ii][ty + 16 * a];
+                for (int a = 0; a < RB; ++a)
 #pragma unroll
-            for (int b = 0; b < RB; ++b) vb[b] = Ms[ii][tx + 16 * b];
+                    for (int b = 0; b < RB; ++b) {
+                        float p, pe, s, se;
+                        two_prod(va[a], vb[b], p, pe);
+                        two_sum(acc[a][b], p, s, se);
+                        acc[a][b] = s;
+                        comp[a][b] += se + pe;       // comp = low-order part
+                    }
+            }
+        } else {
+            float blk[RB][RB];
 #pragma unroll
             for (int a = 0; a < RB; ++a)
 #pragma unroll
-                for (int b = 0; b < RB; ++b) blk[a][b] = fmaf(va[a], vb[b], blk[a][b]);
+                for (int b = 0; b < RB; ++b) blk[a][b] = 0.0f;
+#pragma unroll 4
+            for (int ii = 0; ii < GBK; ++ii) {
+                float va[RB], vb[RB];
+#pragma unroll
+                for (int a = 0; a < RB; ++a) va[a] = Ms[ii][ty + 16 * a];
+#pragma unroll
+                for (int b = 0; b < RB; ++b) vb[b] = Ms[ii][tx + 16 * b];
+#pragma unroll
+                for (int a = 0; a < RB; ++a)
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) blk[a][b] = fmaf(va[a], vb[b], blk[a][b]);
+            }
+#pragma unroll
+            for (int a = 0; a < RB; ++a)
+#pragma unroll
+                for (int b = 0; b < RB; ++b) kahan_add(acc[a][b], comp[a][b], blk[a][b]);
         }
-#pragma unroll
-        for (int a = 0; a < RB; ++a)
-#pragma unroll
-            for (int b = 0; b < RB; ++b) kahan_add(acc[a][b], comp[a][b], blk[a][b]);
         __syncthreads();
     }
     float *out = part + (int64_t)blockIdx.x * rs * rs;
@@ -140,7 +176,14 @@ gram_partial_kernel(const float *__restrict__ M, int64_t N, int64_t ldm, int r,
 #pragma unroll
         for (int b = 0; b < RB; ++b) {
             const int i = ty + 16 * a, j = tx + 16 * b;
-            if (i < rs && j < rs) out[i * rs + j] = acc[a][b] - comp[a][b];
+            if (i < rs && j < rs) {
+                if constexpr (EXACT) {
+                    out[i * rs + j] = acc[a][b];
+                    part_lo[(int64_t)blockIdx.x * rs * rs + i * rs + j] = comp[a][b];
+                } else {
+                    out[i * rs + j] = acc[a][b] - comp[a][b];
+                }
+            }
         }
 }
 
@@ -151,6 +194,25 @@ __global__ void gram_reduce_kernel(const float *__restrict__ part, int nparts, i
     float s = 0.0f, c = 0.0f;
     for (int p = 0; p < nparts; ++p) kahan_add(s, c, part[(int64_t)p * rs * rs + e]);
     G[e] = s - c;
+}
+
+// Pairs (hi_p, lo_p) summed exactly into G + G_lo (hi part rounded to FP32).
+__global__ void gram_reduce_exact_kernel(const float *__restrict__ part,
+                                         const float *__restrict__ part_lo, int nparts, int rs,
+                                         float *__restrict__ G, float *__restrict__ G_lo) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rs * rs) return;
+    float hi = 0.0f, lo = 0.0f;
+    for (int p = 0; p < nparts; ++p) {
+        float s, se;
+        two_sum(hi, part[(int64_t)p * rs * rs + e], s, se);
+        hi = s;
+        lo += se + part_lo[(int64_t)p * rs * rs + e];
+    }
+    float g, ge;
+    two_sum(hi, lo, g, ge);
+    G[e] = g;
+    G_lo[e] = ge;
 }
 
 struct GramPlan {
@@ -169,17 +231,18 @@ GramPlan plan_gram(int64_t N) {
     return p;
 }
 
-template <bool ROWS>
+template <bool ROWS, bool EXACT>
 cudaError_t gram_launch(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
-                        void *ws, cudaStream_t st) {
+                        float *G_lo, void *ws, cudaStream_t st) {
     const GramPlan p = plan_gram(N);
     float *part = static_cast<float *>(ws);
+    float *part_lo = part + (size_t)p.nparts * rs * rs;
     const int rb = (r + 15) / 16;
     switch (rb) {
-#define NMF_GRAM_CASE(RBV)                                                                   \
-    case RBV:                                                                                \
-        gram_partial_kernel<RBV, ROWS><<<p.nparts, 256, 0, st>>>(M, N, ldm, r, p.chunk, part, \
-                                                                 rs);                        \
+#define NMF_GRAM_CASE(RBV)                                                                     \
+    case RBV:                                                                                  \
+        gram_partial_kernel<RBV, ROWS, EXACT><<<p.nparts, 256, 0, st>>>(M, N, ldm, r, p.chunk,  \
+                                                                        part, part_lo, rs);    \
         break;
         NMF_GRAM_CASE(1) NMF_GRAM_CASE(2) NMF_GRAM_CASE(3) NMF_GRAM_CASE(4)
         NMF_GRAM_CASE(5) NMF_GRAM_CASE(6) NMF_GRAM_CASE(7) NMF_GRAM_CASE(8)
@@ -188,31 +251,45 @@ cudaError_t gram_launch(const float *M, int64_t N, int64_t ldm, int r, int rs, f
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    gram_reduce_kernel<<<(rs * rs + 255) / 256, 256, 0, st>>>(part, p.nparts, rs, G);
+    if constexpr (EXACT)
+        gram_reduce_exact_kernel<<<(rs * rs + 255) / 256, 256, 0, st>>>(part, part_lo, p.nparts, rs,
+                                                                        G, G_lo);
+    else
+        gram_reduce_kernel<<<(rs * rs + 255) / 256, 256, 0, st>>>(part, p.nparts, rs, G);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- e(0)
-// Per row i of W: <w_i, c_i> and w_i^T D w_i (FP32 inner products of length
-// r, accumulated across rows in FP64); one partial pair per CTA.
+// Per row i of W, Remark 1 in residual form: <w_i, c_i> and <w_i, D w_i - c_i>
+// with c = C + C_lo, D = D + D_lo; D w - c evaluated with error-free
+// products and sums, both terms accumulated across rows in FP64.
 __global__ void __launch_bounds__(256)
 err_rows_kernel(int64_t m, int r, int rs, const float *__restrict__ W,
-                const float *__restrict__ C, const float *__restrict__ D,
+                const float *__restrict__ C, const float *__restrict__ C_lo,
+                const float *__restrict__ D, const float *__restrict__ D_lo,
                 ErrPartial *__restrict__ part) {
-    extern __shared__ float Ds[];   // rs x rs
+    extern __shared__ float Ds[];   // rs x rs hi, then rs x rs lo
     __shared__ double red[256 / 32];
-    for (int e = threadIdx.x; e < rs * rs; e += blockDim.x) Ds[e] = D[e];
+    for (int e = threadIdx.x; e < rs * rs; e += blockDim.x) {
+        Ds[e] = D[e];
+        Ds[rs * rs + e] = D_lo[e];
+    }
     __syncthreads();
     double cross = 0.0, quad = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float *w = W + i * rs;
-        const float *c = C + i * rs;
         for (int k = 0; k < r; ++k) {
-            float dw = 0.0f;
-            for (int j = 0; j < r; ++j) dw = fmaf(Ds[k * rs + j], w[j], dw);
-            cross = fma((double)w[k], (double)c[k], cross);
-            quad = fma((double)w[k], (double)dw, quad);
+            float hi = -C[i * rs + k], lo = -C_lo[i * rs + k];
+            for (int j = 0; j < r; ++j) {
+                float p, pe, sum, se;
+                two_prod(Ds[k * rs + j], w[j], p, pe);
+                two_sum(hi, p, sum, se);
+                hi = sum;
+                lo += se + pe + Ds[rs * rs + k * rs + j] * w[j];
+            }
+            cross = fma((double)w[k], (double)C[i * rs + k] + (double)C_lo[i * rs + k], cross);
+            quad = fma((double)w[k], (double)hi + (double)lo, quad);
         }
     }
     const double cs = block_sum_d<256>(cross, red);
@@ -233,7 +310,7 @@ __global__ void init_state_kernel(const ErrPartial *__restrict__ part, int npart
         q += part[p].quad;
     }
     const double f = *fro2;
-    const double e2 = f - 2.0 * c + q;
+    const double e2 = f - c + q;      // residual form of Remark 1
     const double e = sqrt(e2 > 0.0 ? e2 : 0.0);
     s->fro2 = f;
     s->e_last = e;
@@ -310,17 +387,17 @@ cudaError_t launch_fro2(const float *vals, int64_t rows, int64_t cols, int64_t l
 
 size_t gram_ws_bytes(int64_t N, int rs) {
     const GramPlan p = plan_gram(N);
-    return sizeof(float) * (size_t)p.nparts * rs * rs;
+    return 2 * sizeof(float) * (size_t)p.nparts * rs * rs;
 }
 
 cudaError_t launch_gram_rows(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
                              void *ws, cudaStream_t st) {
-    return gram_launch<true>(M, N, ldm, r, rs, G, ws, st);
+    return gram_launch<true, false>(M, N, ldm, r, rs, G, nullptr, ws, st);
 }
 
 cudaError_t launch_gram_cols(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
-                             void *ws, cudaStream_t st) {
-    return gram_launch<false>(M, N, ldm, r, rs, G, ws, st);
+                             float *G_lo, void *ws, cudaStream_t st) {
+    return gram_launch<false, true>(M, N, ldm, r, rs, G, G_lo, ws, st);
 }
 
 int err_rows_num_ctas(int64_t m) {
@@ -330,22 +407,24 @@ int err_rows_num_ctas(int64_t m) {
 }
 
 cudaError_t launch_err_rows(int64_t m, int r, int rs, const float *W, const float *C,
-                            const float *D, ErrPartial *part, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)rs * rs;
+                            const float *C_lo, const float *D, const float *D_lo,
+                            ErrPartial *part, cudaStream_t st) {
+    const size_t smem = 2 * sizeof(float) * (size_t)rs * rs;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(err_rows_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    err_rows_kernel<<<err_rows_num_ctas(m), 256, smem, st>>>(m, r, rs, W, C, D, part);
+    err_rows_kernel<<<err_rows_num_ctas(m), 256, smem, st>>>(m, r, rs, W, C, C_lo, D, D_lo, part);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_state(int64_t m, int r, int rs, const float *W, const float *C,
-                              const float *D, const double *fro2, DevState *state,
-                              double beta0, ErrPartial *partials, cudaStream_t st) {
-    cudaError_t e = launch_err_rows(m, r, rs, W, C, D, partials, st);
+                              const float *C_lo, const float *D, const float *D_lo,
+                              const double *fro2, DevState *state, double beta0,
+                              ErrPartial *partials, cudaStream_t st) {
+    cudaError_t e = launch_err_rows(m, r, rs, W, C, C_lo, D, D_lo, partials, st);
     if (e != cudaSuccess) return e;
     init_state_kernel<<<1, 32, 0, st>>>(partials, err_rows_num_ctas(m), fro2, state, beta0);
     return cudaGetLastError();
