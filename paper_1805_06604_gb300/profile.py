@@ -1,0 +1,57 @@
+"""Per-phase device time of E-A-HALS outer iterations on a synthetic workload.
+
+    python -m paper_1805_06604_gb300.profile --workload dense_noisy --iters 2
+
+Creates a solver on cuda:0 for the workload, runs `--warm` graphed
+iterations, then `--iters` ungraphed iterations through nmf_profile_phases
+(a CUDA event between consecutive phases on the solver's stream) and prints
+the mean microseconds of every phase.  Under a profiler, the ungraphed
+iterations launch each kernel of the path once per iteration.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import nmf
+from . import workloads as wl
+
+WORKLOADS = {
+    "dense_noisy": lambda: wl.dense_noisy(0),
+    "image_like": lambda: wl.image_like(0),
+    "document_like": lambda: wl.document_like(0),
+    "oracle_scale": lambda: wl.oracle_scale(0),
+}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense_noisy")
+    ap.add_argument("--iters", type=int, default=2)
+    ap.add_argument("--warm", type=int, default=0)
+    args = ap.parse_args(argv)
+    import numpy as np
+    import torch
+    nmf.load()
+    P = WORKLOADS[args.workload]()
+    st = torch.cuda.current_stream()
+    if P.is_csr:
+        s = nmf.Solver(None, P.r, P.W0.astype(np.float32), P.H0.astype(np.float32),
+                       csr=(P.rowptr, P.colidx, P.val.astype(np.float32)), m=P.m, n=P.n,
+                       stream=st)
+    else:
+        X = torch.from_numpy(P.X.astype(np.float32)).cuda()
+        s = nmf.Solver(X, P.r, torch.from_numpy(P.W0.astype(np.float32)).cuda(),
+                       torch.from_numpy(P.H0.astype(np.float32)).cuda(), stream=st)
+    if args.warm:
+        s.step(args.warm)
+    ms = s.profile_phases(args.iters)
+    info = s.info()
+    s.close()
+    print(json.dumps({"workload": P.name, "lw": info.lw, "lh": info.lh,
+                      "phase_us": {k: round(v * 1000.0, 2) for k, v in ms.items()},
+                      "iteration_us": round(sum(ms.values()) * 1000.0, 2)}))
+
+
+if __name__ == "__main__":
+    main()
