@@ -209,6 +209,21 @@ nmf_status nmf_profile_phases(nmf_handle *h, int32_t iters, double *ms);
  * Synchronises the stream first. */
 nmf_status nmf_destroy(nmf_handle *h);
 
+/* ||X||_F^2 of a device matrix (m x n, row stride ld >= n, FP32), written to
+ * the device double *out on `stream`, without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate at the point of use -- code whose device memory is owned
+ * by another framework's allocator, or latency-critical loops where a
+ * cudaMalloc could block.  Its partial sums live in a fixed 128 KiB
+ * __device__ array inside the library, so: m*n is limited to 2^28 entries
+ * (NMF_ENOTSUP beyond that); calls whose kernels overlap on the GPU race on
+ * that array and must be serialised by the caller; the first call on each
+ * device resolves the array's address (make it before any stream capture).
+ * Inputs and output are the caller's device buffers.  Errors: NMF_EINVAL
+ * for NULL pointers or bad shapes, NMF_ECUDA for launch failures. */
+nmf_status nmf_fro2_noalloc(const float *X, int64_t m, int64_t n, int64_t ld,
+                            double *out, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *nmf_last_error(void);
 

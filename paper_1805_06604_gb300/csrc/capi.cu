@@ -56,6 +56,11 @@ inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+nmf_status nmfg::set_error(nmf_status s, const char *msg) {
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+    return s;
+}
+
 struct nmf_handle {
     cudaStream_t st = nullptr;          // caller's stream
     cudaStream_t cap = nullptr;         // private stream used for graph capture

@@ -153,6 +153,9 @@ cudaError_t launch_wtx_csc(const int64_t *colptr, const int32_t *rowidx, const f
 cudaError_t launch_transpose_h(const float *H, int r, int64_t n, int64_t ldh, float *Ht, int rs,
                                cudaStream_t st);
 
+// Records `msg` as the calling thread's nmf_last_error() and returns s.
+nmf_status set_error(nmf_status s, const char *msg);
+
 // Sets *flag to 1 when v[0..count) holds a NaN or an Inf.
 cudaError_t launch_nonfinite_scan(const float *v, int64_t count, int *flag, cudaStream_t st);
 

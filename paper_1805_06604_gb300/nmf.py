@@ -80,6 +80,8 @@ _SIGS = {
     "nmf_set_state": [ct.c_void_p, ct.POINTER(nmf_scalars), ct.c_void_p, ct.c_void_p,
                       ct.c_void_p, ct.c_void_p, ct.c_int32],
     "nmf_profile_phases": [ct.c_void_p, ct.c_int32, ct.c_void_p],
+    "nmf_fro2_noalloc": [ct.c_void_p, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_void_p,
+                         ct.c_void_p],
     "nmf_destroy": [ct.c_void_p],
 }
 PHASES = ["gram_w", "wtx", "hals_h", "gram_h", "xht", "hals_w", "finalize"]
@@ -285,6 +287,20 @@ def nmf_profile_phases(h, iters: int) -> dict:
     ms = np.zeros(len(PHASES))
     _check(load().nmf_profile_phases(h, int(iters), ms.ctypes.data), "nmf_profile_phases")
     return dict(zip(PHASES, ms.tolist()))
+
+
+def nmf_fro2_noalloc(X, out, stream=None):
+    """||X||_F^2 of a CUDA float32 tensor X (m x n, rows may be strided) into
+    the CUDA float64 tensor `out` (one element), with no device allocation."""
+    if not (_is_torch(X) and X.is_cuda and _is_torch(out) and out.is_cuda):
+        raise TypeError("X and out must be CUDA tensors")
+    import torch
+    if X.dtype != torch.float32 or X.dim() != 2 or X.stride(1) != 1:
+        raise TypeError("X must be a 2-D float32 tensor with unit column stride")
+    if out.dtype != torch.float64 or out.numel() < 1:
+        raise TypeError("out must hold at least one float64")
+    _check(load().nmf_fro2_noalloc(X.data_ptr(), X.shape[0], X.shape[1], X.stride(0),
+                                   out.data_ptr(), _stream_ptr(stream)), "nmf_fro2_noalloc")
 
 
 def nmf_destroy(h):
