@@ -52,9 +52,10 @@ typedef enum { NMF_DENSE = 0, NMF_CSR = 1 } nmf_format;
  * FP64 (Remark 1). */
 typedef enum {
     NMF_PREC_FP32 = 0,   /* FP32 FMA on CUDA cores                            */
-    NMF_PREC_TF32 = 1,   /* TF32 tensor cores (tcgen05), FP32 accumulate      */
-    NMF_PREC_BF16X3 = 2  /* split BF16 (hi/lo pair of X and of the factor),
-                            three tcgen05 products, FP32 accumulate           */
+    NMF_PREC_TF32 = 1,   /* TF32 tensor cores (tcgen05), FP32 accumulate; the
+                            library also keeps X^T (dense X only)             */
+    NMF_PREC_BF16X3 = 2  /* split BF16 (hi/lo pairs of X, X^T and the factor),
+                            three tcgen05 products, FP32 accumulate (dense X) */
 } nmf_precision;
 
 typedef struct {
@@ -204,6 +205,19 @@ typedef enum {
  * ms[NMF_NUM_PHASES].  The iterations advance the solver exactly like
  * nmf_step.  Synchronises the stream. */
 nmf_status nmf_profile_phases(nmf_handle *h, int32_t iters, double *ms);
+
+/* out = P Q^T on the tensor cores, the product kernel of the TF32 and
+ * BF16X3 precision modes (C = X H^T in the solver).  Device pointers: P is
+ * M x K (row stride ldp), Q is q_rows x K (row stride ldq), out is
+ * M x q_rows (row stride ldo), all FP32 row-major; ldp and ldq multiples of
+ * 8; 1 <= q_rows <= 128.  precision is NMF_PREC_TF32 (operands read as
+ * TF32) or NMF_PREC_BF16X3 (P and Q split into hi/lo BF16, three products,
+ * FP32 accumulation).  Allocates its temporaries and synchronises `stream`.
+ * Errors: NMF_EINVAL for bad shapes, NMF_ENOTSUP for other precisions,
+ * NMF_ETIMEOUT when a bounded pipeline wait expired. */
+nmf_status nmf_matmul_nt(const float *P, int64_t M, int64_t K, int64_t ldp, const float *Q,
+                         int32_t q_rows, int64_t ldq, float *out, int64_t ldo,
+                         int32_t precision, void *stream);
 
 /* Releases every device and host resource of the handle (NULL is a no-op).
  * Synchronises the stream first. */

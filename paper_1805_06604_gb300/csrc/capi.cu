@@ -84,6 +84,13 @@ struct nmf_handle {
     float *Wn = nullptr, *Hn = nullptr, *Hw = nullptr;
     float *A = nullptr, *C = nullptr, *G = nullptr, *D = nullptr;
     float *C_lo = nullptr, *D_lo = nullptr;      // low parts for the Remark 1 terms
+    // tensor-core precision modes
+    int64_t ldm = 0;                             // m rounded up to 8
+    float *Xt = nullptr, *Wt = nullptr;          // X^T (n x ldm), W_y^T (rs x ldm)
+    __nv_bfloat16 *Xh = nullptr, *Xl = nullptr, *Xth = nullptr, *Xtl = nullptr;
+    __nv_bfloat16 *Wth = nullptr, *Wtl = nullptr, *Hh = nullptr, *Hl = nullptr;
+    unsigned int *tct_c = nullptr, *tct_a = nullptr;
+    int *tc_err = nullptr;
     double *fro2 = nullptr;
     DevState *state = nullptr;
     ErrPartial *partials = nullptr;
@@ -111,7 +118,8 @@ void free_handle(nmf_handle *h) {
     void *ptrs[] = {h->X, h->rowptr, h->colidx, h->val, h->colptr, h->rowidx, h->cval, h->Ht,
                     h->carry,
                     h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn, h->Hw, h->A, h->C, h->G, h->D,
-                    h->C_lo, h->D_lo,
+                    h->C_lo, h->D_lo, h->Xt, h->Wt, h->Xh, h->Xl, h->Xth, h->Xtl, h->Wth,
+                    h->Wtl, h->Hh, h->Hl, h->tct_c, h->tct_a, h->tc_err,
                     h->fro2, h->state, h->partials, h->counter, h->tickets, h->xtickets, h->ws, h->flag,
                     h->tr_e, h->tr_beta, h->tr_acc};
     for (void *q : ptrs)
@@ -140,13 +148,39 @@ DevParams dev_params(const nmf_handle *h) {
     return d;
 }
 
-// X products for the current layout.
+inline int round16(int r) { return (r + 15) / 16 * 16; }
+
+// X products for the current layout and precision.
 cudaError_t enqueue_wtx(nmf_handle *h, const float *Wsrc, cudaStream_t st) {
     if (h->is_csr)
         return launch_wtx_csc(h->colptr, h->rowidx, h->cval, h->n, h->nnz, h->r, h->rs, Wsrc, h->A,
                               h->ld, h->carry, st);
-    return launch_wtx_f32(h->X, h->m, h->ld, h->ld, h->r, Wsrc, h->rs, h->A, h->ws, h->tickets,
-                          st);
+    if (h->p.precision == NMF_PREC_FP32)
+        return launch_wtx_f32(h->X, h->m, h->ld, h->ld, h->r, Wsrc, h->rs, h->A, h->ws,
+                              h->tickets, st);
+    // A^T = X^T W_y on the tensor cores: W_y^T (rs x ldm) is rebuilt each time.
+    cudaError_t e = launch_transpose(Wsrc, h->m, h->rs, h->rs, h->Wt, h->ldm, st);
+    if (e != cudaSuccess) return e;
+    TcOperands o{};
+    if (h->p.precision == NMF_PREC_BF16X3) {
+        e = launch_split_bf16(h->Wt, h->rs, h->m, h->ldm, h->Wth, h->Wtl, h->ldm, st);
+        if (e != cudaSuccess) return e;
+        o.P = h->Xth;
+        o.P_lo = h->Xtl;
+        o.Q = h->Wth;
+        o.Q_lo = h->Wtl;
+    } else {
+        o.P = h->Xt;
+        o.Q = h->Wt;
+    }
+    o.M = h->n;
+    o.K = h->m;
+    o.ldp = h->ldm;
+    o.ldq = h->ldm;
+    o.q_rows = h->r;
+    o.N = round16(h->r);
+    o.nvalid = h->r;
+    return launch_tc_product(o, h->p.precision, true, h->A, h->ld, h->ws, h->tct_a, h->tc_err, st);
 }
 
 cudaError_t enqueue_xht(nmf_handle *h, const float *Hsrc, cudaStream_t st) {
@@ -156,8 +190,29 @@ cudaError_t enqueue_xht(nmf_handle *h, const float *Hsrc, cudaStream_t st) {
         return launch_xht_csr(h->rowptr, h->colidx, h->val, h->m, h->nnz, h->r, h->rs, h->Ht, h->C,
                               h->carry, st);
     }
-    return launch_xht_f32(h->X, h->m, h->ld, h->r, Hsrc, h->ld, h->C, h->C_lo, h->rs, h->ws,
-                          h->xtickets, st);
+    if (h->p.precision == NMF_PREC_FP32)
+        return launch_xht_f32(h->X, h->m, h->ld, h->r, Hsrc, h->ld, h->C, h->C_lo, h->rs, h->ws,
+                              h->xtickets, st);
+    TcOperands o{};
+    if (h->p.precision == NMF_PREC_BF16X3) {
+        cudaError_t e = launch_split_bf16(Hsrc, h->r, h->n, h->ld, h->Hh, h->Hl, h->ld, st);
+        if (e != cudaSuccess) return e;
+        o.P = h->Xh;
+        o.P_lo = h->Xl;
+        o.Q = h->Hh;
+        o.Q_lo = h->Hl;
+    } else {
+        o.P = h->X;
+        o.Q = Hsrc;
+    }
+    o.M = h->m;
+    o.K = h->n;
+    o.ldp = h->ld;
+    o.ldq = h->ld;
+    o.q_rows = h->r;
+    o.N = round16(h->r);
+    o.nvalid = h->rs;
+    return launch_tc_product(o, h->p.precision, false, h->C, h->rs, h->ws, h->tct_c, h->tc_err, st);
 }
 
 // One outer iteration of Algorithm 2, enqueued on st.  When ev != nullptr,
@@ -277,8 +332,6 @@ nmf_status check_params(const nmf_params *p) {
         if (!(p->alpha > 0.0)) return fail(NMF_EINVAL, "alpha must be > 0");
     if (p->precision < NMF_PREC_FP32 || p->precision > NMF_PREC_BF16X3)
         return fail(NMF_EINVAL, "unknown precision %d", p->precision);
-    if (p->precision != NMF_PREC_FP32)
-        return fail(NMF_ENOTSUP, "precision %d is not available in this build", p->precision);
     return NMF_OK;
 }
 
@@ -392,6 +445,12 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
         return fail(NMF_ECUDA, "no CUDA device is available (this library has no CPU path)");
     }
 
+    if (p.precision != NMF_PREC_FP32) {
+        if (X->format == NMF_CSR)
+            return fail(NMF_ENOTSUP, "tensor-core precisions need a dense X");
+        if (!tc_available())
+            return fail(NMF_ENOTSUP, "the tensor-map driver entry point is unavailable");
+    }
     nmf_handle *h = new (std::nothrow) nmf_handle();
     if (!h) return fail(NMF_ENOMEM, "host allocation failed");
     h->st = static_cast<cudaStream_t>(stream);
@@ -400,6 +459,7 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     h->r = r;
     h->rs = (int)round_up(r, 8);
     h->ld = round_up(X->n, 8);
+    h->ldm = round_up(X->m, 8);
     h->is_csr = X->format == NMF_CSR;
     h->nnz = h->is_csr ? X->nnz : X->m * X->n;
     h->p = p;
@@ -450,6 +510,9 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     size_t ws = std::max(gram_ws_bytes(m, (int)rs), gram_ws_bytes(n, (int)rs));
     ws = std::max(ws, fro2_ws_bytes(m * ld));
     if (!h->is_csr) ws = std::max({ws, wtx_ws_bytes(m, ld, r), xht_ws_bytes(m, ld, r)});
+    if (p.precision != NMF_PREC_FP32)
+        ws = std::max({ws, tc_ws_bytes(m, n, round16(r), p.precision),
+                       tc_ws_bytes(n, m, round16(r), p.precision)});
     h->ws_bytes = ws;
     NMF_TRYC(cudaMalloc(&h->ws, ws));
 
@@ -534,6 +597,36 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
             return fail(NMF_ENONFINITE, "X holds a NaN or Inf");
         }
         NMF_TRYC(launch_fro2(h->X, m, ld, ld, h->fro2, h->ws, st));
+        if (p.precision != NMF_PREC_FP32) {
+            // X^T for the W^T X product (and hi/lo BF16 copies of X and X^T).
+            NMF_TRYC(dalloc(&h->Xt, n * h->ldm));
+            NMF_TRYC(cudaMemsetAsync(h->Xt, 0, sizeof(float) * n * h->ldm, st));
+            NMF_TRYC(launch_transpose(h->X, m, n, ld, h->Xt, h->ldm, st));
+            NMF_TRYC(dalloc(&h->Wt, rs * h->ldm));
+            NMF_TRYC(cudaMemsetAsync(h->Wt, 0, sizeof(float) * rs * h->ldm, st));
+            NMF_TRYC(dalloc(&h->tct_c, tc_num_tickets(m)));
+            NMF_TRYC(dalloc(&h->tct_a, tc_num_tickets(n)));
+            NMF_TRYC(dalloc(&h->tc_err, 1));
+            NMF_TRYC(cudaMemsetAsync(h->tct_c, 0, sizeof(unsigned int) * tc_num_tickets(m), st));
+            NMF_TRYC(cudaMemsetAsync(h->tct_a, 0, sizeof(unsigned int) * tc_num_tickets(n), st));
+            NMF_TRYC(cudaMemsetAsync(h->tc_err, 0, sizeof(int), st));
+            if (p.precision == NMF_PREC_BF16X3) {
+                NMF_TRYC(dalloc(&h->Xh, m * ld));
+                NMF_TRYC(dalloc(&h->Xl, m * ld));
+                NMF_TRYC(dalloc(&h->Xth, n * h->ldm));
+                NMF_TRYC(dalloc(&h->Xtl, n * h->ldm));
+                NMF_TRYC(dalloc(&h->Wth, rs * h->ldm));
+                NMF_TRYC(dalloc(&h->Wtl, rs * h->ldm));
+                NMF_TRYC(dalloc(&h->Hh, r * ld));
+                NMF_TRYC(dalloc(&h->Hl, r * ld));
+                NMF_TRYC(launch_split_bf16(h->X, m, ld, ld, h->Xh, h->Xl, ld, st));
+                NMF_TRYC(launch_split_bf16(h->Xt, n, h->ldm, h->ldm, h->Xth, h->Xtl, h->ldm, st));
+                NMF_TRYC(cudaMemsetAsync(h->Wth, 0, sizeof(__nv_bfloat16) * rs * h->ldm, st));
+                NMF_TRYC(cudaMemsetAsync(h->Wtl, 0, sizeof(__nv_bfloat16) * rs * h->ldm, st));
+                NMF_TRYC(cudaMemsetAsync(h->Hh, 0, sizeof(__nv_bfloat16) * r * ld, st));
+                NMF_TRYC(cudaMemsetAsync(h->Hl, 0, sizeof(__nv_bfloat16) * r * ld, st));
+            }
+        }
     }
 
     // e(0) = ||X - W H||_F via Remark 1 (Algorithm 2 step 1).
@@ -584,6 +677,13 @@ nmf_status nmf_get_info(nmf_handle *h, nmf_info *info) {
     // W sweeps (1) + finalize (1); CSR: each product is 2 kernels (+ a
     // memset) and X H^T adds the H transpose.
     info->launches_per_iter = h->is_csr ? 12 : 9;
+    if (h->p.precision == NMF_PREC_TF32) info->launches_per_iter = 10;     // + W_y transpose
+    if (h->p.precision == NMF_PREC_BF16X3) info->launches_per_iter = 12;   // + transpose, 2 splits
+    if (h->tc_err) {
+        int e = 0;
+        NMF_CUDA(cudaMemcpy(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e && info->device_status == 0) info->device_status = (int32_t)NMF_ETIMEOUT;
+    }
     return NMF_OK;
 }
 
@@ -756,6 +856,71 @@ nmf_status nmf_profile_phases(nmf_handle *h, int32_t iters, double *ms) {
     for (int i = 0; i <= NMF_NUM_PHASES; ++i) cudaEventDestroy(ev[i]);
     if (out != NMF_OK) return out;
     for (int i = 0; i < NMF_NUM_PHASES; ++i) ms[i] = acc[i] / iters;
+    return NMF_OK;
+}
+
+nmf_status nmf_matmul_nt(const float *P, int64_t M, int64_t K, int64_t ldp, const float *Q,
+                         int32_t q_rows, int64_t ldq, float *out, int64_t ldo, int32_t precision,
+                         void *stream) {
+    if (!P || !Q || !out || M < 1 || K < 1 || q_rows < 1 || q_rows > kMaxRank || ldp < K ||
+        ldq < K || ldo < q_rows || ldp % 8 || ldq % 8)
+        return fail(NMF_EINVAL, "nmf_matmul_nt: bad pointers or shapes (ld must be multiples of 8)");
+    if (precision != NMF_PREC_TF32 && precision != NMF_PREC_BF16X3)
+        return fail(NMF_ENOTSUP, "nmf_matmul_nt runs the tensor-core precisions only");
+    if (!tc_available()) return fail(NMF_ENOTSUP, "the tensor-map driver entry point is unavailable");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int N = round16(q_rows);
+    void *ws = nullptr;
+    unsigned int *tickets = nullptr;
+    int *err = nullptr;
+    __nv_bfloat16 *ph = nullptr, *pl = nullptr, *qh = nullptr, *ql = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(ws);
+        cudaFree(tickets);
+        cudaFree(err);
+        cudaFree(ph);
+        cudaFree(pl);
+        cudaFree(qh);
+        cudaFree(ql);
+    };
+    const size_t wsb = tc_ws_bytes(M, K, N, precision);
+    cudaError_t e = cudaMalloc(&ws, wsb);
+    if (e == cudaSuccess) e = cudaMalloc(&tickets, sizeof(unsigned int) * tc_num_tickets(M));
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, sizeof(unsigned int) * tc_num_tickets(M), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    TcOperands o{};
+    o.M = M;
+    o.K = K;
+    o.ldp = ldp;
+    o.ldq = ldq;
+    o.q_rows = q_rows;
+    o.N = N;
+    o.nvalid = q_rows;
+    if (e == cudaSuccess && precision == NMF_PREC_BF16X3) {
+        e = cudaMalloc(&ph, sizeof(__nv_bfloat16) * M * ldp);
+        if (e == cudaSuccess) e = cudaMalloc(&pl, sizeof(__nv_bfloat16) * M * ldp);
+        if (e == cudaSuccess) e = cudaMalloc(&qh, sizeof(__nv_bfloat16) * q_rows * ldq);
+        if (e == cudaSuccess) e = cudaMalloc(&ql, sizeof(__nv_bfloat16) * q_rows * ldq);
+        if (e == cudaSuccess) e = launch_split_bf16(P, M, K, ldp, ph, pl, ldp, st);
+        if (e == cudaSuccess) e = launch_split_bf16(Q, q_rows, K, ldq, qh, ql, ldq, st);
+        o.P = ph;
+        o.P_lo = pl;
+        o.Q = qh;
+        o.Q_lo = ql;
+    } else {
+        o.P = P;
+        o.Q = Q;
+    }
+    if (e == cudaSuccess) e = launch_tc_product(o, precision, false, out, ldo, ws, tickets, err, st);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? NMF_ENOMEM : NMF_ECUDA, "nmf_matmul_nt: %s",
+                    cudaGetErrorString(e));
+    if (flag) return fail(NMF_ETIMEOUT, "nmf_matmul_nt: a bounded tensor-core pipeline wait expired");
     return NMF_OK;
 }
 

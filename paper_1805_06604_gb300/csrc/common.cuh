@@ -2,6 +2,7 @@
 // libnmf_gb300 (never included by the oracle or by callers).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -152,6 +153,27 @@ cudaError_t launch_wtx_csc(const int64_t *colptr, const int32_t *rowidx, const f
                            int64_t lda, float *carry, cudaStream_t st);
 cudaError_t launch_transpose_h(const float *H, int r, int64_t n, int64_t ldh, float *Ht, int rs,
                                cudaStream_t st);
+
+// Tensor-core products (tc_products.cu): out = P Q^T, P (M x K) and Q
+// (q_rows x K) K-major in FP32 (TF32 mode) or as BF16 hi/lo pairs (BF16X3
+// mode); N = q_rows rounded up to 16 (<= 128); nvalid columns are written.
+// transposed_out writes out[col * out_ld + row].
+struct TcOperands {
+    const void *P, *P_lo, *Q, *Q_lo;
+    int64_t M, K, ldp, ldq;
+    int q_rows, N, nvalid;
+};
+size_t tc_ws_bytes(int64_t M, int64_t K, int N, int precision);
+int64_t tc_num_tickets(int64_t M);
+bool tc_available();
+cudaError_t launch_tc_product(const TcOperands &o, int precision, bool transposed_out, float *out,
+                              int64_t out_ld, void *ws, unsigned int *tickets, int *err_flag,
+                              cudaStream_t st);
+cudaError_t launch_split_bf16(const float *x, int64_t rows, int64_t cols, int64_t ld,
+                              __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ld_out,
+                              cudaStream_t st);
+cudaError_t launch_transpose(const float *in, int64_t rows, int64_t cols, int64_t ld_in,
+                             float *out, int64_t ld_out, cudaStream_t st);
 
 // Records `msg` as the calling thread's nmf_last_error() and returns s.
 nmf_status set_error(nmf_status s, const char *msg);

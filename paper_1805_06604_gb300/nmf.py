@@ -80,6 +80,8 @@ _SIGS = {
     "nmf_set_state": [ct.c_void_p, ct.POINTER(nmf_scalars), ct.c_void_p, ct.c_void_p,
                       ct.c_void_p, ct.c_void_p, ct.c_int32],
     "nmf_profile_phases": [ct.c_void_p, ct.c_int32, ct.c_void_p],
+    "nmf_matmul_nt": [ct.c_void_p, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_void_p, ct.c_int32,
+                      ct.c_int64, ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p],
     "nmf_fro2_noalloc": [ct.c_void_p, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_void_p,
                          ct.c_void_p],
     "nmf_destroy": [ct.c_void_p],
@@ -287,6 +289,17 @@ def nmf_profile_phases(h, iters: int) -> dict:
     ms = np.zeros(len(PHASES))
     _check(load().nmf_profile_phases(h, int(iters), ms.ctypes.data), "nmf_profile_phases")
     return dict(zip(PHASES, ms.tolist()))
+
+
+def nmf_matmul_nt(P, Q, out, precision, stream=None):
+    """out = P Q^T on the tensor cores for CUDA float32 tensors P (M x K),
+    Q (q x K) and out (M x q); row strides must be multiples of 8."""
+    for t in (P, Q, out):
+        if not (_is_torch(t) and t.is_cuda and t.stride(1) == 1):
+            raise TypeError("P, Q, out must be CUDA tensors with unit column stride")
+    _check(load().nmf_matmul_nt(P.data_ptr(), P.shape[0], P.shape[1], P.stride(0), Q.data_ptr(),
+                                Q.shape[0], Q.stride(0), out.data_ptr(), out.stride(0),
+                                int(precision), _stream_ptr(stream)), "nmf_matmul_nt")
 
 
 def nmf_fro2_noalloc(X, out, stream=None):

@@ -29,12 +29,15 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense_noisy")
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--warm", type=int, default=0)
+    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16x3"], default="fp32")
     args = ap.parse_args(argv)
     import numpy as np
     import torch
     nmf.load()
     P = WORKLOADS[args.workload]()
     st = torch.cuda.current_stream()
+    prec = {"fp32": nmf.NMF_PREC_FP32, "tf32": nmf.NMF_PREC_TF32,
+            "bf16x3": nmf.NMF_PREC_BF16X3}[args.precision]
     if P.is_csr:
         s = nmf.Solver(None, P.r, P.W0.astype(np.float32), P.H0.astype(np.float32),
                        csr=(P.rowptr, P.colidx, P.val.astype(np.float32)), m=P.m, n=P.n,
@@ -42,13 +45,15 @@ def main(argv=None):
     else:
         X = torch.from_numpy(P.X.astype(np.float32)).cuda()
         s = nmf.Solver(X, P.r, torch.from_numpy(P.W0.astype(np.float32)).cuda(),
-                       torch.from_numpy(P.H0.astype(np.float32)).cuda(), stream=st)
+                       torch.from_numpy(P.H0.astype(np.float32)).cuda(), stream=st,
+                       precision=prec)
     if args.warm:
         s.step(args.warm)
     ms = s.profile_phases(args.iters)
     info = s.info()
     s.close()
-    print(json.dumps({"workload": P.name, "lw": info.lw, "lh": info.lh,
+    print(json.dumps({"workload": P.name, "precision": args.precision, "lw": info.lw,
+                      "lh": info.lh, "device_status": info.device_status,
                       "phase_us": {k: round(v * 1000.0, 2) for k, v in ms.items()},
                       "iteration_us": round(sum(ms.values()) * 1000.0, 2)}))
 
