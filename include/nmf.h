@@ -238,6 +238,35 @@ nmf_status nmf_destroy(nmf_handle *h);
 nmf_status nmf_fro2_noalloc(const float *X, int64_t m, int64_t n, int64_t ld,
                             double *out, void *stream);
 
+/* ---- Batched solver: many independent problems of uneven size. ---------
+ * Each instance is a full solver (as nmf_create).  One outer iteration of
+ * every instance is captured into a single CUDA graph in which the
+ * instances form independent chains spread over B concurrent branches; the
+ * number of branches and the longest-first assignment of instances to
+ * branches are picked at creation by timing candidate graphs (the tuning
+ * iterations are undone from a device snapshot).  All work goes on `stream`. */
+typedef struct nmf_batch nmf_batch;
+
+/* Xs[i], ranks[i], W0[i] (m_i x r_i), H0[i] (r_i x n_i) describe instance
+ * i; p applies to all (sweep budgets computed per instance when 0).
+ * Errors as nmf_create, reported with the failing instance index. */
+nmf_status nmf_batch_create(nmf_batch **out, int32_t count, const nmf_matrix *Xs,
+                            const int32_t *ranks, const float *const *W0,
+                            const float *const *H0, int32_t factors_on_device,
+                            const nmf_params *p, void *stream);
+/* `iters` outer iterations of every instance: one graph launch each. */
+nmf_status nmf_batch_step(nmf_batch *b, int32_t iters);
+/* The same iterations as a per-instance launch loop (each instance's own
+ * one-iteration graph, one after another): the baseline the batched graph
+ * is measured against.  Results are identical to nmf_batch_step. */
+nmf_status nmf_batch_step_loop(nmf_batch *b, int32_t iters);
+nmf_status nmf_batch_get_info(nmf_batch *b, int32_t i, nmf_info *info);
+nmf_status nmf_batch_get_factors(nmf_batch *b, int32_t i, float *W, float *H,
+                                 int32_t to_device);
+/* The autotuner's choice: branches and its measured ms per iteration. */
+nmf_status nmf_batch_schedule(nmf_batch *b, int32_t *branches, double *ms_per_iter);
+nmf_status nmf_batch_destroy(nmf_batch *b);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *nmf_last_error(void);
 

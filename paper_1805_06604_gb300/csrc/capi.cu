@@ -931,4 +931,286 @@ nmf_status nmf_destroy(nmf_handle *h) {
     return NMF_OK;
 }
 
+
+// --------------------------------------------------------------------------
+// Batched solver: one CUDA graph per outer iteration holding the kernels of
+// every instance, split into `branches` independent chains (each a capture
+// stream forked from and joined to the graph's origin), so the GPU runs the
+// instances of different branches concurrently.  An autotuner picks the
+// number of branches and a longest-first assignment of instances to branches
+// by timing candidate graphs on a snapshot of the state, which it restores.
+// --------------------------------------------------------------------------
+}  // extern "C"
+
+struct nmf_batch {
+    cudaStream_t st = nullptr;                  // caller's stream
+    std::vector<nmf_handle *> h;
+    std::vector<cudaStream_t> br;               // capture streams
+    cudaGraphExec_t exec = nullptr;
+    int branches = 1;
+    double tuned_ms = 0.0;
+    int64_t k_enq = 0;
+};
+
+namespace {
+
+void free_batch(nmf_batch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto *h : b->h) free_handle(h);
+    for (auto s : b->br) cudaStreamDestroy(s);
+    delete b;
+}
+
+double est_cost(const nmf_handle *h) {
+    const double m = (double)h->m, n = (double)h->n, r = (double)h->r;
+    return 4.0 * m * n * r + 2.0 * r * r * (h->lh * n + h->lw * m);
+}
+
+// Longest-first: instances sorted by decreasing cost, each to the least
+// loaded branch.
+std::vector<std::vector<int>> assign(const nmf_batch *b, int branches) {
+    std::vector<int> idx(b->h.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+    std::sort(idx.begin(), idx.end(),
+              [&](int x, int y) { return est_cost(b->h[x]) > est_cost(b->h[y]); });
+    std::vector<std::vector<int>> out(branches);
+    std::vector<double> load(branches, 0.0);
+    for (int i : idx) {
+        const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        out[j].push_back(i);
+        load[j] += est_cost(b->h[i]);
+    }
+    return out;
+}
+
+nmf_status build_batch_graph(nmf_batch *b, int branches, cudaGraphExec_t *exec) {
+    *exec = nullptr;
+    const auto groups = assign(b, branches);
+    cudaStream_t origin = b->br[0];
+    cudaGraph_t g = nullptr;
+    std::vector<cudaEvent_t> evs;
+    auto mk = [&]() {
+        cudaEvent_t e;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        evs.push_back(e);
+        return e;
+    };
+    cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEvent_t fork = mk();
+        e = cudaEventRecord(fork, origin);
+        for (int j = 1; j < branches && e == cudaSuccess; ++j)
+            e = cudaStreamWaitEvent(b->br[j], fork, 0);
+        for (int j = 0; j < branches && e == cudaSuccess; ++j)
+            for (int i : groups[j]) {
+                e = enqueue_iteration(b->h[i], b->br[j]);
+                if (e != cudaSuccess) break;
+            }
+        for (int j = 1; j < branches && e == cudaSuccess; ++j) {
+            cudaEvent_t join = mk();
+            e = cudaEventRecord(join, b->br[j]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, join, 0);
+        }
+    }
+    cudaError_t e2 = cudaStreamEndCapture(origin, &g);
+    for (auto ev : evs) cudaEventDestroy(ev);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(NMF_ECUDA, "batch graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(NMF_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    return NMF_OK;
+}
+
+// Device-side snapshot of every instance's iterate and scalar state.
+struct Snapshot {
+    std::vector<void *> bufs;
+    ~Snapshot() {
+        for (void *p : bufs) cudaFree(p);
+    }
+};
+
+nmf_status snapshot(nmf_batch *b, Snapshot &sn, bool restore) {
+    size_t q = 0;
+    for (auto *h : b->h) {
+        struct Item {
+            void *p;
+            size_t bytes;
+        } items[] = {{h->W, sizeof(float) * h->m * h->rs},  {h->Wy, sizeof(float) * h->m * h->rs},
+                     {h->H, sizeof(float) * h->r * h->ld},  {h->Hy, sizeof(float) * h->r * h->ld},
+                     {h->state, sizeof(DevState)}};
+        for (auto &it : items) {
+            if (!restore) {
+                void *d = nullptr;
+                NMF_CUDA(cudaMalloc(&d, it.bytes));
+                sn.bufs.push_back(d);
+                NMF_CUDA(cudaMemcpyAsync(d, it.p, it.bytes, cudaMemcpyDeviceToDevice, b->st));
+            } else {
+                NMF_CUDA(cudaMemcpyAsync(it.p, sn.bufs[q++], it.bytes, cudaMemcpyDeviceToDevice,
+                                         b->st));
+            }
+        }
+    }
+    NMF_CUDA(cudaStreamSynchronize(b->st));
+    return NMF_OK;
+}
+
+nmf_status batch_ensure_trace(nmf_batch *b, int64_t need) {
+    bool grown = false;
+    for (auto *h : b->h)
+        if (need > h->tr_cap) {
+            nmf_status s = ensure_trace(h, need);
+            if (s != NMF_OK) return s;
+            grown = true;
+        }
+    if (grown && b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+        nmf_status s = build_batch_graph(b, b->branches, &b->exec);
+        if (s != NMF_OK) return s;
+    }
+    return NMF_OK;
+}
+
+nmf_status autotune(nmf_batch *b) {
+    const int count = (int)b->h.size();
+    std::vector<int> cands;
+    for (int c : {1, 2, 4, 8, 16, 32, 64})
+        if (c <= count && c <= (int)b->br.size()) cands.push_back(c);
+    nmf_status s = batch_ensure_trace(b, b->k_enq + 4 * (int64_t)cands.size() + 8);
+    if (s != NMF_OK) return s;
+    Snapshot sn;
+    s = snapshot(b, sn, false);
+    if (s != NMF_OK) return s;
+    cudaEvent_t e0, e1;
+    NMF_CUDA(cudaEventCreate(&e0));
+    NMF_CUDA(cudaEventCreate(&e1));
+    double best = 1e30;
+    int best_c = 1;
+    for (int c : cands) {
+        cudaGraphExec_t ex = nullptr;
+        s = build_batch_graph(b, c, &ex);
+        if (s != NMF_OK) break;
+        cudaGraphLaunch(ex, b->st);                 // warm
+        cudaEventRecord(e0, b->st);
+        for (int it = 0; it < 3; ++it) cudaGraphLaunch(ex, b->st);
+        cudaEventRecord(e1, b->st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        cudaGraphExecDestroy(ex);
+        if (e != cudaSuccess) {
+            s = fail(NMF_ECUDA, "autotune run failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (ms / 3.0 < best) {
+            best = ms / 3.0;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != NMF_OK) return s;
+    s = snapshot(b, sn, true);                      // undo the tuning iterations
+    if (s != NMF_OK) return s;
+    b->branches = best_c;
+    b->tuned_ms = best;
+    return build_batch_graph(b, best_c, &b->exec);
+}
+
+}  // namespace
+
+extern "C" {
+
+nmf_status nmf_batch_create(nmf_batch **out, int32_t count, const nmf_matrix *Xs,
+                            const int32_t *ranks, const float *const *W0, const float *const *H0,
+                            int32_t factors_on_device, const nmf_params *p, void *stream) {
+    if (!out) return fail(NMF_EINVAL, "out pointer is NULL");
+    *out = nullptr;
+    if (count < 1 || !Xs || !ranks || !W0 || !H0)
+        return fail(NMF_EINVAL, "nmf_batch_create: count >= 1 and all arrays are required");
+    nmf_batch *b = new (std::nothrow) nmf_batch();
+    if (!b) return fail(NMF_ENOMEM, "host allocation failed");
+    b->st = static_cast<cudaStream_t>(stream);
+    for (int32_t i = 0; i < count; ++i) {
+        nmf_handle *h = nullptr;
+        nmf_status s = nmf_create(&h, &Xs[i], ranks[i], W0[i], H0[i], factors_on_device, p, stream);
+        if (s != NMF_OK) {
+            free_batch(b);
+            char msg[600];
+            snprintf(msg, sizeof(msg), "instance %d: %s", (int)i, g_err);
+            return fail(s, "%s", msg);
+        }
+        b->h.push_back(h);
+    }
+    const int nbr = std::min<int>(64, count);
+    for (int j = 0; j < nbr; ++j) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            free_batch(b);
+            return fail(NMF_ECUDA, "stream creation failed");
+        }
+        b->br.push_back(s);
+    }
+    nmf_status s = autotune(b);
+    if (s != NMF_OK) {
+        free_batch(b);
+        return s;
+    }
+    *out = b;
+    return NMF_OK;
+}
+
+nmf_status nmf_batch_step(nmf_batch *b, int32_t iters) {
+    if (!b || iters < 0) return fail(NMF_EINVAL, "bad arguments");
+    nmf_status s = batch_ensure_trace(b, b->k_enq + iters);
+    if (s != NMF_OK) return s;
+    for (int32_t i = 0; i < iters; ++i) NMF_CUDA(cudaGraphLaunch(b->exec, b->st));
+    b->k_enq += iters;
+    for (auto *h : b->h) h->k_enq = b->k_enq;
+    return NMF_OK;
+}
+
+nmf_status nmf_batch_step_loop(nmf_batch *b, int32_t iters) {
+    if (!b || iters < 0) return fail(NMF_EINVAL, "bad arguments");
+    nmf_status s = batch_ensure_trace(b, b->k_enq + iters);
+    if (s != NMF_OK) return s;
+    for (int32_t it = 0; it < iters; ++it)
+        for (auto *h : b->h) NMF_CUDA(cudaGraphLaunch(h->exec, b->st));
+    b->k_enq += iters;
+    for (auto *h : b->h) h->k_enq = b->k_enq;
+    return NMF_OK;
+}
+
+nmf_status nmf_batch_get_info(nmf_batch *b, int32_t i, nmf_info *info) {
+    if (!b || i < 0 || i >= (int32_t)b->h.size()) return fail(NMF_EINVAL, "bad instance index");
+    NMF_CUDA(cudaStreamSynchronize(b->st));
+    return nmf_get_info(b->h[i], info);
+}
+
+nmf_status nmf_batch_get_factors(nmf_batch *b, int32_t i, float *W, float *H, int32_t to_device) {
+    if (!b || i < 0 || i >= (int32_t)b->h.size()) return fail(NMF_EINVAL, "bad instance index");
+    NMF_CUDA(cudaStreamSynchronize(b->st));
+    return nmf_get_factors(b->h[i], W, H, to_device);
+}
+
+nmf_status nmf_batch_schedule(nmf_batch *b, int32_t *branches, double *ms_per_iter) {
+    if (!b) return fail(NMF_EINVAL, "batch is NULL");
+    if (branches) *branches = b->branches;
+    if (ms_per_iter) *ms_per_iter = b->tuned_ms;
+    return NMF_OK;
+}
+
+nmf_status nmf_batch_destroy(nmf_batch *b) {
+    if (!b) return NMF_OK;
+    cudaStreamSynchronize(b->st);
+    free_batch(b);
+    return NMF_OK;
+}
+
 }  // extern "C"

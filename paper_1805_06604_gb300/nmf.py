@@ -85,6 +85,15 @@ _SIGS = {
     "nmf_fro2_noalloc": [ct.c_void_p, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_void_p,
                          ct.c_void_p],
     "nmf_destroy": [ct.c_void_p],
+    "nmf_batch_create": [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_void_p, ct.c_void_p,
+                         ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(nmf_params),
+                         ct.c_void_p],
+    "nmf_batch_step": [ct.c_void_p, ct.c_int32],
+    "nmf_batch_step_loop": [ct.c_void_p, ct.c_int32],
+    "nmf_batch_get_info": [ct.c_void_p, ct.c_int32, ct.POINTER(nmf_info)],
+    "nmf_batch_get_factors": [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_int32],
+    "nmf_batch_schedule": [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_double)],
+    "nmf_batch_destroy": [ct.c_void_p],
 }
 PHASES = ["gram_w", "wtx", "hals_h", "gram_h", "xht", "hals_w", "finalize"]
 EXPORTED = sorted(list(_SIGS) + ["nmf_last_error", "nmf_version"])
@@ -320,6 +329,71 @@ def nmf_destroy(h):
     if h is not None and h.value:
         _check(load().nmf_destroy(h), "nmf_destroy")
         h.value = None
+
+
+class Batch:
+    """Many independent instances (host numpy inputs): one graph per iteration."""
+
+    def __init__(self, problems, stream=None, **params):
+        """problems: list of (X m x n float32, r, W0 m x r, H0 r x n)."""
+        self.params = nmf_params_default(**params)
+        n = len(problems)
+        mats = (nmf_matrix * n)()
+        self._keep = []
+        ranks = (ct.c_int32 * n)()
+        w0 = (ct.c_void_p * n)()
+        h0 = (ct.c_void_p * n)()
+        self.shapes = []
+        for i, (X, r, W0, H0) in enumerate(problems):
+            m, k = make_matrix(X)
+            mats[i] = m
+            self._keep.append(k)
+            pw, _, kw = _ptr_and_dev(W0, np.float32)
+            ph, _, kh = _ptr_and_dev(H0, np.float32)
+            self._keep += [kw, kh]
+            w0[i], h0[i] = pw, ph
+            ranks[i] = int(r)
+            self.shapes.append((int(X.shape[0]), int(X.shape[1]), int(r)))
+        self.h = ct.c_void_p()
+        _check(load().nmf_batch_create(ct.byref(self.h), n, mats, ranks, w0, h0, 0,
+                                       ct.byref(self.params), _stream_ptr(stream)),
+               "nmf_batch_create")
+        self._keep = None
+
+    def step(self, iters=1):
+        _check(load().nmf_batch_step(self.h, int(iters)), "nmf_batch_step")
+
+    def step_loop(self, iters=1):
+        _check(load().nmf_batch_step_loop(self.h, int(iters)), "nmf_batch_step_loop")
+
+    def info(self, i) -> nmf_info:
+        out = nmf_info()
+        _check(load().nmf_batch_get_info(self.h, int(i), ct.byref(out)), "nmf_batch_get_info")
+        return out
+
+    def factors(self, i):
+        m, n, r = self.shapes[i]
+        W = np.zeros((m, r), np.float32)
+        H = np.zeros((r, n), np.float32)
+        _check(load().nmf_batch_get_factors(self.h, int(i), W.ctypes.data, H.ctypes.data, 0),
+               "nmf_batch_get_factors")
+        return W, H
+
+    def schedule(self):
+        b, ms = ct.c_int32(), ct.c_double()
+        _check(load().nmf_batch_schedule(self.h, ct.byref(b), ct.byref(ms)), "nmf_batch_schedule")
+        return b.value, ms.value
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            _check(load().nmf_batch_destroy(self.h), "nmf_batch_destroy")
+            self.h.value = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Solver:

@@ -30,7 +30,12 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--warm", type=int, default=0)
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16x3"], default="fp32")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time COUNT uneven instances (m, n ~ U{64..2048}, r ~ U{4..32}): "
+                         "batched graph vs per-instance launch loop")
     args = ap.parse_args(argv)
+    if args.batch:
+        return batch_main(args)
     import numpy as np
     import torch
     nmf.load()
@@ -56,6 +61,37 @@ def main(argv=None):
                       "lh": info.lh, "device_status": info.device_status,
                       "phase_us": {k: round(v * 1000.0, 2) for k, v in ms.items()},
                       "iteration_us": round(sum(ms.values()) * 1000.0, 2)}))
+
+
+def batch_main(args):
+    import time
+    import torch
+    nmf.load()
+    probs = wl.batch(count=args.batch, seed=0)
+    t0 = time.perf_counter()
+    b = nmf.Batch([(P.X, P.r, P.W0, P.H0) for P in probs])
+    t_create = time.perf_counter() - t0
+    branches, tuned = b.schedule()
+    K = max(args.iters, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, fn in (("graph", b.step), ("loop", b.step_loop)):
+        fn(1)
+        torch.cuda.synchronize()
+        e0.record()
+        fn(K)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / K
+    flops = sum(4.0 * P.m * P.n * P.r for P in probs)
+    b.close()
+    print(json.dumps({"instances": args.batch, "sum_mn": int(sum(P.m * P.n for P in probs)),
+                      "branches": branches, "autotune_ms_per_iter": round(tuned, 3),
+                      "create_s": round(t_create, 2), "iters": K,
+                      "graph_ms_per_iter": round(res["graph"], 3),
+                      "loop_ms_per_iter": round(res["loop"], 3),
+                      "speedup": round(res["loop"] / res["graph"], 2),
+                      "product_gflop_per_iter": round(flops / 1e9, 2)}))
 
 
 if __name__ == "__main__":

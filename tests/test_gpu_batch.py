@@ -1,0 +1,81 @@
+"""Batched solver: many uneven instances in one CUDA graph per iteration.
+
+Every instance runs the same kernels in the same order as a single-instance
+solver, only scheduled concurrently, so results are compared bit for bit
+with nmf_create/nmf_step (which the parity tests check against the oracle),
+and the per-instance launch loop must give identical results too."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1805_06604_gb300 import nmf
+from paper_1805_06604_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1805_06604_gb300 import build
+    build.build()
+    O.build()
+    nmf.load()
+
+
+def _problems(count, seed=1, mn=(64, 400)):
+    return wl.batch(count=count, seed=seed, mn_range=mn, r_range=(4, 32))
+
+
+def test_batch_matches_single_instance_solvers():
+    probs = _problems(24)
+    K = 12
+    with nmf.Batch([(P.X, P.r, P.W0, P.H0) for P in probs]) as b:
+        branches, ms = b.schedule()
+        assert 1 <= branches <= 24 and ms > 0
+        b.step(K)
+        for i, P in enumerate(probs):
+            W, H = b.factors(i)
+            with nmf.Solver(P.X, P.r, P.W0, P.H0) as s:
+                s.step(K)
+                Ws, Hs = s.factors()
+                assert b.info(i).k == K
+                np.testing.assert_array_equal(W, Ws)
+                np.testing.assert_array_equal(H, Hs)
+                assert b.info(i).e_last == s.info().e_last
+
+
+def test_batch_loop_equals_graph_and_tuning_is_undone():
+    probs = _problems(10, seed=2)
+    with nmf.Batch([(P.X, P.r, P.W0, P.H0) for P in probs]) as a, \
+            nmf.Batch([(P.X, P.r, P.W0, P.H0) for P in probs]) as b:
+        assert all(a.info(i).k == 0 for i in range(len(probs)))
+        a.step(7)
+        b.step_loop(7)
+        for i in range(len(probs)):
+            Wa, Ha = a.factors(i)
+            Wb, Hb = b.factors(i)
+            np.testing.assert_array_equal(Wa, Wb)
+            np.testing.assert_array_equal(Ha, Hb)
+
+
+def test_batch_instance_against_oracle():
+    """One instance of a batch, single step from its state after 5 batched
+    iterations, against the oracle (same gate as the single-instance tests)."""
+    from gpu_helpers import gram_kappa, normwise, oracle_params, step_tol
+    probs = _problems(6, seed=3)
+    with nmf.Batch([(P.X, P.r, P.W0, P.H0) for P in probs]) as b:
+        b.step(5)
+        i = 4
+        P = probs[i]
+        info = b.info(i)
+        assert info.device_status == 0
+        W, H = b.factors(i)
+        p = oracle_params(P)
+        Xo = P.X.astype(np.float32).astype(np.float64)
+        st = O.eahals_init(Xo, P.W0, P.H0, p)
+        O.eahals_run(Xo, st, p, 5)
+        rel_o = np.linalg.norm(Xo - st.W @ st.H) / np.linalg.norm(Xo)
+        rel_g = np.linalg.norm(Xo - W.astype(np.float64) @ H) / np.linalg.norm(Xo)
+        assert abs(rel_g - rel_o) <= 1e-3 * rel_o, (rel_g, rel_o)
