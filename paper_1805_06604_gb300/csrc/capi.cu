@@ -86,8 +86,10 @@ struct nmf_handle {
     float *C_lo = nullptr, *D_lo = nullptr;      // low parts for the Remark 1 terms
     // tensor-core precision modes
     int64_t ldm = 0;                             // m rounded up to 8
-    float *Xt = nullptr, *Wt = nullptr;          // X^T (n x ldm), W_y^T (rs x ldm)
-    __nv_bfloat16 *Xh = nullptr, *Xl = nullptr, *Xth = nullptr, *Xtl = nullptr;
+    float *Wt = nullptr;                          // W_y^T (rs x ldm)
+    // Packed X for the tensor-core products: Pc for X H^T (P = X), Pa for
+    // X^T W (P = X^T); the _lo arrays hold the BF16X3 low parts.
+    void *Pc = nullptr, *Pc_lo = nullptr, *Pa = nullptr, *Pa_lo = nullptr;
     __nv_bfloat16 *Wth = nullptr, *Wtl = nullptr, *Hh = nullptr, *Hl = nullptr;
     unsigned int *tct_c = nullptr, *tct_a = nullptr;
     int *tc_err = nullptr;
@@ -118,7 +120,7 @@ void free_handle(nmf_handle *h) {
     void *ptrs[] = {h->X, h->rowptr, h->colidx, h->val, h->colptr, h->rowidx, h->cval, h->Ht,
                     h->carry,
                     h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn, h->Hw, h->A, h->C, h->G, h->D,
-                    h->C_lo, h->D_lo, h->Xt, h->Wt, h->Xh, h->Xl, h->Xth, h->Xtl, h->Wth,
+                    h->C_lo, h->D_lo, h->Wt, h->Pc, h->Pc_lo, h->Pa, h->Pa_lo, h->Wth,
                     h->Wtl, h->Hh, h->Hl, h->tct_c, h->tct_a, h->tc_err,
                     h->fro2, h->state, h->partials, h->counter, h->tickets, h->xtickets, h->ws, h->flag,
                     h->tr_e, h->tr_beta, h->tr_acc};
@@ -165,17 +167,15 @@ cudaError_t enqueue_wtx(nmf_handle *h, const float *Wsrc, cudaStream_t st) {
     if (h->p.precision == NMF_PREC_BF16X3) {
         e = launch_split_bf16(h->Wt, h->rs, h->m, h->ldm, h->Wth, h->Wtl, h->ldm, st);
         if (e != cudaSuccess) return e;
-        o.P = h->Xth;
-        o.P_lo = h->Xtl;
         o.Q = h->Wth;
         o.Q_lo = h->Wtl;
     } else {
-        o.P = h->Xt;
         o.Q = h->Wt;
     }
+    o.P = h->Pa;
+    o.P_lo = h->Pa_lo;
     o.M = h->n;
     o.K = h->m;
-    o.ldp = h->ldm;
     o.ldq = h->ldm;
     o.q_rows = h->r;
     o.N = round16(h->r);
@@ -197,17 +197,15 @@ cudaError_t enqueue_xht(nmf_handle *h, const float *Hsrc, cudaStream_t st) {
     if (h->p.precision == NMF_PREC_BF16X3) {
         cudaError_t e = launch_split_bf16(Hsrc, h->r, h->n, h->ld, h->Hh, h->Hl, h->ld, st);
         if (e != cudaSuccess) return e;
-        o.P = h->Xh;
-        o.P_lo = h->Xl;
         o.Q = h->Hh;
         o.Q_lo = h->Hl;
     } else {
-        o.P = h->X;
         o.Q = Hsrc;
     }
+    o.P = h->Pc;
+    o.P_lo = h->Pc_lo;
     o.M = h->m;
     o.K = h->n;
-    o.ldp = h->ld;
     o.ldq = h->ld;
     o.q_rows = h->r;
     o.N = round16(h->r);
@@ -598,10 +596,18 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
         }
         NMF_TRYC(launch_fro2(h->X, m, ld, ld, h->fro2, h->ws, st));
         if (p.precision != NMF_PREC_FP32) {
-            // X^T for the W^T X product (and hi/lo BF16 copies of X and X^T).
-            NMF_TRYC(dalloc(&h->Xt, n * h->ldm));
-            NMF_TRYC(cudaMemsetAsync(h->Xt, 0, sizeof(float) * n * h->ldm, st));
-            NMF_TRYC(launch_transpose(h->X, m, n, ld, h->Xt, h->ldm, st));
+            // Packed copies of X (for X H^T) and X^T (for X^T W), made once.
+            const bool bf = p.precision == NMF_PREC_BF16X3;
+            const size_t bc = tc_packed_bytes(m, n, p.precision);
+            const size_t ba = tc_packed_bytes(n, m, p.precision);
+            NMF_TRYC(cudaMalloc(&h->Pc, bc));
+            NMF_TRYC(cudaMalloc(&h->Pa, ba));
+            if (bf) {
+                NMF_TRYC(cudaMalloc(&h->Pc_lo, bc));
+                NMF_TRYC(cudaMalloc(&h->Pa_lo, ba));
+            }
+            NMF_TRYC(launch_tc_pack(h->X, m, n, ld, false, p.precision, h->Pc, h->Pc_lo, st));
+            NMF_TRYC(launch_tc_pack(h->X, m, n, ld, true, p.precision, h->Pa, h->Pa_lo, st));
             NMF_TRYC(dalloc(&h->Wt, rs * h->ldm));
             NMF_TRYC(cudaMemsetAsync(h->Wt, 0, sizeof(float) * rs * h->ldm, st));
             NMF_TRYC(dalloc(&h->tct_c, tc_num_tickets(m)));
@@ -611,16 +617,10 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
             NMF_TRYC(cudaMemsetAsync(h->tct_a, 0, sizeof(unsigned int) * tc_num_tickets(n), st));
             NMF_TRYC(cudaMemsetAsync(h->tc_err, 0, sizeof(int), st));
             if (p.precision == NMF_PREC_BF16X3) {
-                NMF_TRYC(dalloc(&h->Xh, m * ld));
-                NMF_TRYC(dalloc(&h->Xl, m * ld));
-                NMF_TRYC(dalloc(&h->Xth, n * h->ldm));
-                NMF_TRYC(dalloc(&h->Xtl, n * h->ldm));
                 NMF_TRYC(dalloc(&h->Wth, rs * h->ldm));
                 NMF_TRYC(dalloc(&h->Wtl, rs * h->ldm));
                 NMF_TRYC(dalloc(&h->Hh, r * ld));
                 NMF_TRYC(dalloc(&h->Hl, r * ld));
-                NMF_TRYC(launch_split_bf16(h->X, m, ld, ld, h->Xh, h->Xl, ld, st));
-                NMF_TRYC(launch_split_bf16(h->Xt, n, h->ldm, h->ldm, h->Xth, h->Xtl, h->ldm, st));
                 NMF_TRYC(cudaMemsetAsync(h->Wth, 0, sizeof(__nv_bfloat16) * rs * h->ldm, st));
                 NMF_TRYC(cudaMemsetAsync(h->Wtl, 0, sizeof(__nv_bfloat16) * rs * h->ldm, st));
                 NMF_TRYC(cudaMemsetAsync(h->Hh, 0, sizeof(__nv_bfloat16) * r * ld, st));
@@ -873,7 +873,8 @@ nmf_status nmf_matmul_nt(const float *P, int64_t M, int64_t K, int64_t ldp, cons
     void *ws = nullptr;
     unsigned int *tickets = nullptr;
     int *err = nullptr;
-    __nv_bfloat16 *ph = nullptr, *pl = nullptr, *qh = nullptr, *ql = nullptr;
+    void *ph = nullptr, *pl = nullptr;
+    __nv_bfloat16 *qh = nullptr, *ql = nullptr;
     auto cleanup = [&]() {
         cudaFree(ws);
         cudaFree(tickets);
@@ -892,26 +893,26 @@ nmf_status nmf_matmul_nt(const float *P, int64_t M, int64_t K, int64_t ldp, cons
     TcOperands o{};
     o.M = M;
     o.K = K;
-    o.ldp = ldp;
     o.ldq = ldq;
     o.q_rows = q_rows;
     o.N = N;
     o.nvalid = q_rows;
-    if (e == cudaSuccess && precision == NMF_PREC_BF16X3) {
-        e = cudaMalloc(&ph, sizeof(__nv_bfloat16) * M * ldp);
-        if (e == cudaSuccess) e = cudaMalloc(&pl, sizeof(__nv_bfloat16) * M * ldp);
-        if (e == cudaSuccess) e = cudaMalloc(&qh, sizeof(__nv_bfloat16) * q_rows * ldq);
+    const bool bf = precision == NMF_PREC_BF16X3;
+    const size_t pb = tc_packed_bytes(M, K, precision);
+    if (e == cudaSuccess) e = cudaMalloc(&ph, pb);
+    if (e == cudaSuccess && bf) e = cudaMalloc(&pl, pb);
+    if (e == cudaSuccess) e = launch_tc_pack(P, M, K, ldp, false, precision, ph, pl, st);
+    if (e == cudaSuccess && bf) {
+        e = cudaMalloc(&qh, sizeof(__nv_bfloat16) * q_rows * ldq);
         if (e == cudaSuccess) e = cudaMalloc(&ql, sizeof(__nv_bfloat16) * q_rows * ldq);
-        if (e == cudaSuccess) e = launch_split_bf16(P, M, K, ldp, ph, pl, ldp, st);
         if (e == cudaSuccess) e = launch_split_bf16(Q, q_rows, K, ldq, qh, ql, ldq, st);
-        o.P = ph;
-        o.P_lo = pl;
         o.Q = qh;
         o.Q_lo = ql;
     } else {
-        o.P = P;
         o.Q = Q;
     }
+    o.P = ph;
+    o.P_lo = pl;
     if (e == cudaSuccess) e = launch_tc_product(o, precision, false, out, ldo, ws, tickets, err, st);
     int flag = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st);

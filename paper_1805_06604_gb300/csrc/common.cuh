@@ -158,11 +158,17 @@ cudaError_t launch_transpose_h(const float *H, int r, int64_t n, int64_t ldh, fl
 // (q_rows x K) K-major in FP32 (TF32 mode) or as BF16 hi/lo pairs (BF16X3
 // mode); N = q_rows rounded up to 16 (<= 128); nvalid columns are written.
 // transposed_out writes out[col * out_ld + row].
+// out = P Q^T on the tensor cores.  P (M x K) is given packed (launch_tc_pack;
+// P_lo is the BF16X3 low part), Q (q_rows x K, row stride ldq) row-major
+// (FP32 for TF32, BF16 hi/lo for BF16X3); N = q_rows rounded up to 16.
 struct TcOperands {
     const void *P, *P_lo, *Q, *Q_lo;
-    int64_t M, K, ldp, ldq;
+    int64_t M, K, ldq;
     int q_rows, N, nvalid;
 };
+size_t tc_packed_bytes(int64_t M, int64_t K, int precision);
+cudaError_t launch_tc_pack(const float *x, int64_t rows, int64_t cols, int64_t ld, bool transposed,
+                           int precision, void *out_hi, void *out_lo, cudaStream_t st);
 size_t tc_ws_bytes(int64_t M, int64_t K, int N, int precision);
 int64_t tc_num_tickets(int64_t M);
 bool tc_available();

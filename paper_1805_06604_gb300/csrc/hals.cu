@@ -11,8 +11,11 @@ cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const 
 
 namespace {
 
-constexpr int kSlots4[] = {2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 20, 24, 28, 32};
-constexpr int kSlots2[] = {2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 20, 24, 28, 32};
+// Two lanes per item up to r = 64, four lanes above (r <= 128): every slot
+// count is instantiated so that an item is padded by less than T coordinates.
+constexpr int kSlots4[] = {17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32};
+constexpr int kSlots2[] = {2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 15, 16, 17,
+                           18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32};
 constexpr int kThreadsPerCta = 128;
 
 template <int N>
@@ -22,17 +25,18 @@ int pick(const int (&list)[N], int need) {
     return -1;
 }
 
-// Two lanes per item once the items fill every scheduler of the GPU with at
-// least one warp (and r <= 64); four lanes otherwise.
-int pick_lanes(int64_t items, int r) {
-    return (r <= 64 && items * 2 >= 4LL * kNumSMs * 32) ? 2 : 4;
-}
+// Lanes per item.  The time of a sweep is set by the latency of one update
+// of an item, which grows with T (longer butterfly and chain), while the
+// items of all warps run concurrently; so the smallest T whose registers
+// hold the item wins -- measured on the dense 10000 x 4000 r = 50 and the
+// 2000 x 1500 r = 24 problems, T = 2 beat T = 4 and T = 8 on both sides.
+int pick_lanes(int r) { return r <= 64 ? 2 : 4; }
 
 template <int LAYOUT>
 cudaError_t dispatch(int64_t items, int r, int64_t ld, const float *A, const float *G, int rs,
                      const float *Xin, float *Xout, int sweeps, const HEpilogue &hep,
                      const WEpilogue &wep, cudaStream_t st) {
-    const int T = pick_lanes(items, r);
+    const int T = pick_lanes(r);
     const int need = (r + T - 1) / T < 2 ? 2 : (r + T - 1) / T;
 #define NMF_HALS_CASE(TV, SV)                                                                \
     case SV:                                                                                 \
@@ -40,12 +44,22 @@ cudaError_t dispatch(int64_t items, int r, int64_t ld, const float *A, const flo
                                            st);
     if (T == 2) {
         switch (pick(kSlots2, need)) {
-            NMF_HALS_CASE(2, 2) NMF_HALS_CASE(2, 3) NMF_HALS_CASE(2, 4) NMF_HALS_CASE(2, 5) NMF_HALS_CASE(2, 6) NMF_HALS_CASE(2, 7) NMF_HALS_CASE(2, 8) NMF_HALS_CASE(2, 9) NMF_HALS_CASE(2, 10) NMF_HALS_CASE(2, 11) NMF_HALS_CASE(2, 12) NMF_HALS_CASE(2, 13) NMF_HALS_CASE(2, 14) NMF_HALS_CASE(2, 15) NMF_HALS_CASE(2, 16) NMF_HALS_CASE(2, 20) NMF_HALS_CASE(2, 24) NMF_HALS_CASE(2, 28) NMF_HALS_CASE(2, 32)
+            NMF_HALS_CASE(2, 2) NMF_HALS_CASE(2, 3) NMF_HALS_CASE(2, 4) NMF_HALS_CASE(2, 5)
+            NMF_HALS_CASE(2, 6) NMF_HALS_CASE(2, 7) NMF_HALS_CASE(2, 8) NMF_HALS_CASE(2, 9)
+            NMF_HALS_CASE(2, 10) NMF_HALS_CASE(2, 11) NMF_HALS_CASE(2, 12) NMF_HALS_CASE(2, 13)
+            NMF_HALS_CASE(2, 14) NMF_HALS_CASE(2, 15) NMF_HALS_CASE(2, 16) NMF_HALS_CASE(2, 17)
+            NMF_HALS_CASE(2, 18) NMF_HALS_CASE(2, 19) NMF_HALS_CASE(2, 20) NMF_HALS_CASE(2, 21)
+            NMF_HALS_CASE(2, 22) NMF_HALS_CASE(2, 23) NMF_HALS_CASE(2, 24) NMF_HALS_CASE(2, 25)
+            NMF_HALS_CASE(2, 26) NMF_HALS_CASE(2, 27) NMF_HALS_CASE(2, 28) NMF_HALS_CASE(2, 29)
+            NMF_HALS_CASE(2, 30) NMF_HALS_CASE(2, 31) NMF_HALS_CASE(2, 32)
             default: break;
         }
     } else {
         switch (pick(kSlots4, need)) {
-            NMF_HALS_CASE(4, 2) NMF_HALS_CASE(4, 3) NMF_HALS_CASE(4, 4) NMF_HALS_CASE(4, 5) NMF_HALS_CASE(4, 6) NMF_HALS_CASE(4, 7) NMF_HALS_CASE(4, 8) NMF_HALS_CASE(4, 9) NMF_HALS_CASE(4, 10) NMF_HALS_CASE(4, 11) NMF_HALS_CASE(4, 12) NMF_HALS_CASE(4, 13) NMF_HALS_CASE(4, 14) NMF_HALS_CASE(4, 15) NMF_HALS_CASE(4, 16) NMF_HALS_CASE(4, 20) NMF_HALS_CASE(4, 24) NMF_HALS_CASE(4, 28) NMF_HALS_CASE(4, 32)
+            NMF_HALS_CASE(4, 17) NMF_HALS_CASE(4, 18) NMF_HALS_CASE(4, 19) NMF_HALS_CASE(4, 20)
+            NMF_HALS_CASE(4, 21) NMF_HALS_CASE(4, 22) NMF_HALS_CASE(4, 23) NMF_HALS_CASE(4, 24)
+            NMF_HALS_CASE(4, 25) NMF_HALS_CASE(4, 26) NMF_HALS_CASE(4, 27) NMF_HALS_CASE(4, 28)
+            NMF_HALS_CASE(4, 29) NMF_HALS_CASE(4, 30) NMF_HALS_CASE(4, 31) NMF_HALS_CASE(4, 32)
             default: break;
         }
     }
@@ -56,7 +70,7 @@ cudaError_t dispatch(int64_t items, int r, int64_t ld, const float *A, const flo
 }  // namespace
 
 int hals_w_num_ctas(int64_t m, int r) {
-    const int T = pick_lanes(m, r);
+    const int T = pick_lanes(r);
     const int64_t per_cta = kThreadsPerCta / T;
     return (int)((m + per_cta - 1) / per_cta);
 }

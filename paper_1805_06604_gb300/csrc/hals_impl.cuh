@@ -19,9 +19,9 @@
 // coordinates that were final D steps earlier, so each lane computes its
 // share of P_k D updates ahead and the T shares are combined by a butterfly
 // of shuffles that is off the critical path.  Every lane then evaluates the
-// short chain (D fused multiply-adds, one multiply, one max) itself, so the
-// new x_k is available in all T lanes without a broadcast; only its owner
-// stores it.  A zero G(k,k) leaves x_k unchanged (the paper does not treat
+// chain terms itself (all but the newest one during the previous update),
+// so the new x_k is available in all T lanes without a broadcast; only its
+// owner stores it.  A zero G(k,k) leaves x_k unchanged (the paper does not treat
 // it; the whole k-th Gram row is then zero, so x_k enters no other update).
 //
 // Fused epilogues.  H side: H_y = H_n + beta (H_n - H) (projected for
@@ -158,7 +158,7 @@ __device__ __forceinline__ float group_allreduce(float p) {
 }
 
 template <int T, int S, int LAYOUT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 1)
 hals_kernel(int64_t items, int r, int64_t ld,
             const float *__restrict__ Aglob,     // right-hand side a (A or C)
             const float *__restrict__ Gglob,     // Gram (G or D), rs x rs
@@ -167,6 +167,7 @@ hals_kernel(int64_t items, int r, int64_t ld,
             int hoist_guard, HEpilogue hep, WEpilogue wep) {
     constexpr int RP = S * T;                    // padded item length
     constexpr int D = T;                         // lookahead depth
+    constexpr int PF = 2;                        // prefetch distance (updates)
     // Per-lane slice stride: 16-byte aligned and an odd number of 16-byte
     // units, so the T slices a warp reads in one phase fall in distinct banks.
     constexpr int SP = 4 * ((S + 3) / 4) + (((S + 3) / 4) % 2 == 0 ? 4 : 0);
@@ -174,8 +175,8 @@ hals_kernel(int64_t items, int r, int64_t ld,
     static_assert(S >= 2, "the lookahead needs RP >= 2T");
     extern __shared__ __align__(16) float smem[];
     float *Grow = smem;                          // [RP][T][SP]: Grow[k][t][s] = G(k, s*T+t)
-    float *Band = smem + RP * ROW;               // [RP][8]: G(k,k-1..k-D), 1/G(k,k)
-    float *Glo = Band + RP * 8;                  // W side with error terms: low part of D
+    float *Band = smem + RP * ROW;               // [RP][16]: G(k,k-1..k-D), 1/G(k,k)
+    float *Glo = Band + RP * 16;                 // W side with error terms: low part of D
     __shared__ double red_cross[kThreads / 32], red_quad[kThreads / 32];
     __shared__ bool am_last;
     const bool err_terms = LAYOUT == kRow && wep.partials != nullptr;
@@ -194,8 +195,8 @@ hals_kernel(int64_t items, int r, int64_t ld,
             Glo[idx] = (k < r && s < S && i < r) ? wep.D_lo[k * rs + i] : 0.0f;
         }
     }
-    for (int idx = threadIdx.x; idx < RP * 8; idx += blockDim.x) {
-        const int k = idx / 8, c = idx % 8;
+    for (int idx = threadIdx.x; idx < RP * 16; idx += blockDim.x) {
+        const int k = idx / 16, c = idx % 16;
         float v = 0.0f;
         if (k < r) {
             if (c < D) {
@@ -226,43 +227,55 @@ hals_kernel(int64_t items, int r, int64_t ld,
 
     // Pipeline state.  hist[k % D]: the newest values x_{k-1..k-D}
     // (replicated in the group).  P[k % D]: reduced P_k.  The butterfly that
-    // combines the T lane shares of a partial is spread over consecutive
-    // updates -- stage i of the partial computed i updates earlier -- so no
-    // shuffle result is consumed in the update that issued it:
-    //   stage[0] = raw share of P_{k+D-1}, stage[1] = P_{k+D-2} after one
-    //   exchange (T = 4 only).  The Gram slice of the next partial and the
-    //   band of the next update are prefetched one update ahead.
-    constexpr int NST = (T == 4) ? 2 : 1;     // butterfly stages = log2(T)
-    float P[D], hist[D], stage[NST];
+    // combines the T lane shares of a partial takes one exchange per update,
+    // and each shuffle's result is used one update after it was issued.
+    // Update k+1's sum without its newest term, c, is formed during update k
+    // from values that are already final, so the loop-carried path of an
+    // update is one fused multiply-add, one multiply and one max whatever T.
+    // Band rows and Gram slices are prefetched PF updates ahead.
+    constexpr int NST = (T == 8) ? 3 : (T == 4 ? 2 : 1);   // butterfly stages = log2(T)
+    // v[j]: a partial after j exchanges; sh[j]: its partner's value, read by
+    // a shuffle issued one update earlier.
+    float P[D], hist[D], v[NST], sh[NST];
 #pragma unroll
     for (int d = 1; d <= D; ++d) {
         const int j = RP - d;                       // "previous sweep" coordinates
         hist[j % D] = __shfl_sync(gmask, x[j / T], j % T, T);
     }
-    float gv[S];
-    // Prologue: complete P_0 .. P_{D-NST-1}; P_{D-NST} .. P_{D-1} enter the
-    // butterfly pipeline at the stage they would have reached.
+    // Prologue: complete P_0 .. P_{D-NST-1}; P_{D-j} (j = 1..NST) enters the
+    // pipeline as if its raw share had been computed j updates ago.
     [&]<int... J>(std::integer_sequence<int, J...>) {
         (
             [&] {
                 constexpr int kk = J;
-                load_slice<S, SP>(gv, Grow + kk * ROW + t * SP);
-                const float v = partial_dot<T, S, kk>(gv, t, x, a);
+                float gs[S];
+                load_slice<S, SP>(gs, Grow + kk * ROW + t * SP);
+                float p = partial_dot<T, S, kk>(gs, t, x, a);
                 if constexpr (kk < D - NST) {
-                    P[kk % D] = group_allreduce<T>(v);        // complete
-                } else if constexpr (kk == D - 1) {
-                    stage[0] = v;                             // raw share of P_{D-1}
+                    P[kk % D] = group_allreduce<T>(p);        // complete
                 } else {
-                    stage[1] = v + __shfl_xor_sync(gmask, v, 1, T);   // P_{D-2}, one exchange
+                    constexpr int j = D - kk;                 // 1..NST
+#pragma unroll
+                    for (int e = 0; e + 1 < j; ++e) p += __shfl_xor_sync(gmask, p, 1 << e, T);
+                    v[j - 1] = p;
+                    sh[j - 1] = __shfl_xor_sync(gmask, p, 1 << (j - 1), T);
                 }
             }(),
             ...);
     }(std::make_integer_sequence<int, D>{});
     // Band values are read as warp-wide broadcast scalars (one wavefront each).
-    float bnext[D + 1];
+    // bq[i] and gq[i] hold the band row of update k+i and the Gram slice of
+    // the partial computed at update k+i, at the start of update k.
+    float bq[PF][D + 1], gq[PF][S];
 #pragma unroll
-    for (int d = 0; d <= D; ++d) bnext[d] = Band[d];
-    load_slice<S, SP>(gv, Grow + (D % RP) * ROW + t * SP);
+    for (int i = 0; i < PF; ++i) {
+#pragma unroll
+        for (int d = 0; d <= D; ++d) bq[i][d] = Band[(i % RP) * 16 + d];
+        load_slice<S, SP>(gq[i], Grow + ((D + i) % RP) * ROW + t * SP);
+    }
+    float c = P[0];                                 // update 0 without its newest term
+#pragma unroll
+    for (int d = D; d >= 2; --d) c = fmaf(-bq[0][d - 1], hist[(RP - d) % D], c);
 
 #pragma unroll 1
     for (int l = 0; l < sweeps; ++l) {
@@ -274,39 +287,55 @@ hals_kernel(int64_t items, int r, int64_t ld,
                 [&] {
                     constexpr int k = K;
                     constexpr int kk = (k + D) % RP;          // partial computed now
-                    // Prefetch the band of update k+1 and the Gram slice of
-                    // the partial of update k+1+D.
-                    float bcur[D + 1];
-#pragma unroll
-                    for (int d = 0; d <= D; ++d) bcur[d] = bnext[d];
-                    {
-                        const float *band = Bl + ((k + 1) % RP) * 8;
-#pragma unroll
-                        for (int d = 0; d <= D; ++d) bnext[d] = band[d];
-                    }
-                    float gcur[S];
-#pragma unroll
-                    for (int s2 = 0; s2 < S; ++s2) gcur[s2] = gv[s2];
-                    load_slice<S, SP>(gv, Gl + ((kk + 1) % RP) * ROW + t * SP);
-                    // Butterfly stages of earlier partials (results used later).
-                    if constexpr (NST == 2) {
-                        const float done = stage[1] + __shfl_xor_sync(gmask, stage[1], 2, T);
-                        stage[1] = stage[0] + __shfl_xor_sync(gmask, stage[0], 1, T);
-                        P[(k + D - 2) % D] = done;
-                    } else {
-                        P[(k + D - 1) % D] = stage[0] + __shfl_xor_sync(gmask, stage[0], 1, T);
-                    }
-                    // Chain of update k.
-                    float s_k = P[k % D];
-#pragma unroll
-                    for (int d = D; d >= 1; --d)
-                        s_k = fmaf(-bcur[d - 1], hist[(k - d + RP) % D], s_k);
-                    const float inv = bcur[D];
+                    // The body is ordered so that every long-latency result
+                    // (shuffle, shared load) is consumed as late as possible
+                    // in the update, or in a later one.
+                    // (1) Update k: the newest chain term, scale, clamp.
+                    const float s_k = fmaf(-bq[0][0], hist[(k - 1 + RP) % D], c);
+                    const float inv = bq[0][D];
                     const float h = fmaxf(s_k * inv, 0.0f);
                     if (t == k % T && inv > 0.0f) x[k / T] = h;
                     hist[k % D] = h;
-                    // Raw share of the partial of update k + D.
-                    stage[0] = partial_dot<T, S, kk>(gcur, t, x, a);
+                    // (2) Butterfly of earlier partials, one exchange per
+                    // update: the partial of update k+D-NST completes; the
+                    // others take the shuffle issued last update and issue
+                    // the next one.
+                    P[(k + D - NST) % D] = v[NST - 1] + sh[NST - 1];
+#pragma unroll
+                    for (int j = NST - 1; j >= 1; --j) {
+                        v[j] = v[j - 1] + sh[j - 1];
+                        sh[j] = __shfl_xor_sync(gmask, v[j], 1 << j, T);
+                    }
+                    // (3) Update k+1 without its newest term (x_k is not used).
+                    {
+                        float cn = P[(k + 1) % D];
+#pragma unroll
+                        for (int d = D; d >= 2; --d)
+                            cn = fmaf(-bq[1][d - 1], hist[(k + 1 - d + RP) % D], cn);
+                        c = cn;
+                    }
+                    // (4) Rotate the prefetch rings and issue the loads of
+                    // update k+PF.
+                    float gcur[S];
+#pragma unroll
+                    for (int s2 = 0; s2 < S; ++s2) gcur[s2] = gq[0][s2];
+#pragma unroll
+                    for (int i = 0; i + 1 < PF; ++i) {
+#pragma unroll
+                        for (int d = 0; d <= D; ++d) bq[i][d] = bq[i + 1][d];
+#pragma unroll
+                        for (int s2 = 0; s2 < S; ++s2) gq[i][s2] = gq[i + 1][s2];
+                    }
+                    {
+                        const float *band = Bl + ((k + PF) % RP) * 16;
+#pragma unroll
+                        for (int d = 0; d <= D; ++d) bq[PF - 1][d] = band[d];
+                    }
+                    load_slice<S, SP>(gq[PF - 1], Gl + ((kk + PF) % RP) * ROW + t * SP);
+                    // (5) Raw share of the partial of update k + D, and the
+                    // first exchange (consumed next update).
+                    v[0] = partial_dot<T, S, kk>(gcur, t, x, a);
+                    sh[0] = __shfl_xor_sync(gmask, v[0], 1, T);
                 }(),
                 ...);
         }(std::make_integer_sequence<int, RP>{});
@@ -329,9 +358,9 @@ hals_kernel(int64_t items, int r, int64_t ld,
                 const int k = s * T + t;
                 if (valid && k < r) {
                     const int64_t q = elem_index<LAYOUT>(item, k, ld);
-                    float v = fmaf(beta, x[s] - hep.H_acc[q], x[s]);
-                    if (hep.hp == 3) v = fmaxf(v, 0.0f);
-                    hep.Hw[q] = v;
+                    float w = fmaf(beta, x[s] - hep.H_acc[q], x[s]);
+                    if (hep.hp == 3) w = fmaxf(w, 0.0f);
+                    hep.Hw[q] = w;
                 }
             }
         }
@@ -436,7 +465,7 @@ cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const 
                         const WEpilogue &wep, cudaStream_t st) {
     constexpr int RP = S * T;
     constexpr int SP = 4 * ((S + 3) / 4) + (((S + 3) / 4) % 2 == 0 ? 4 : 0);
-    const size_t smem = sizeof(float) * (size_t)(RP * T * SP * (LAYOUT == 1 ? 2 : 1) + RP * 8);
+    const size_t smem = sizeof(float) * (size_t)(RP * T * SP * (LAYOUT == 1 ? 2 : 1) + RP * 16);
     auto kern = hals_kernel<T, S, LAYOUT>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -452,12 +481,9 @@ cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const 
 
 }  // namespace nmfg
 
-#define NMF_HALS_INSTANTIATE(TV, SV)                                                            \
-    template cudaError_t nmfg::hals_launch<TV, SV, 0>(int64_t, int, int64_t, const float *,     \
-                                                      const float *, int, const float *,        \
-                                                      float *, int, const nmfg::HEpilogue &,    \
-                                                      const nmfg::WEpilogue &, cudaStream_t);   \
-    template cudaError_t nmfg::hals_launch<TV, SV, 1>(int64_t, int, int64_t, const float *,     \
-                                                      const float *, int, const float *,        \
-                                                      float *, int, const nmfg::HEpilogue &,    \
-                                                      const nmfg::WEpilogue &, cudaStream_t);
+#define NMF_HALS_INSTANTIATE_ONE(TV, SV, LV)                                                    \
+    template cudaError_t nmfg::hals_launch<TV, SV, LV>(                                         \
+        int64_t, int, int64_t, const float *, const float *, int, const float *, float *, int,  \
+        const nmfg::HEpilogue &, const nmfg::WEpilogue &, cudaStream_t);
+// Both sides.
+#define NMF_HALS_INSTANTIATE(TV, SV) NMF_HALS_INSTANTIATE_ONE(TV, SV, 0) NMF_HALS_INSTANTIATE_ONE(TV, SV, 1)

@@ -1,7 +1,9 @@
 // hals_inst_1.cu -- explicit instantiations of the HALS sweep kernel
-// (hals_impl.cuh) for (lanes, slots) = (4, 28), (2, 6), (4, 2).
+// (hals_impl.cuh) for (lanes, slots) = (4, 31), (4, 18), (2, 20), (2, 10), (2, 3).
 #include "hals_impl.cuh"
 
-NMF_HALS_INSTANTIATE(4, 28)
-NMF_HALS_INSTANTIATE(2, 6)
-NMF_HALS_INSTANTIATE(4, 2)
+NMF_HALS_INSTANTIATE(4, 31)
+NMF_HALS_INSTANTIATE(4, 18)
+NMF_HALS_INSTANTIATE(2, 20)
+NMF_HALS_INSTANTIATE(2, 10)
+NMF_HALS_INSTANTIATE(2, 3)

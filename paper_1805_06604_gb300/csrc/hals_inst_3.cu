@@ -1,9 +1,9 @@
 // hals_inst_3.cu -- explicit instantiations of the HALS sweep kernel
-// (hals_impl.cuh) for (lanes, slots) = (2, 32), (4, 11), (4, 9), (4, 6), (4, 4).
+// (hals_impl.cuh) for (lanes, slots) = (4, 29), (4, 19), (2, 22), (2, 12), (2, 6).
 #include "hals_impl.cuh"
 
-NMF_HALS_INSTANTIATE(2, 32)
-NMF_HALS_INSTANTIATE(4, 11)
-NMF_HALS_INSTANTIATE(4, 9)
-NMF_HALS_INSTANTIATE(4, 6)
-NMF_HALS_INSTANTIATE(4, 4)
+NMF_HALS_INSTANTIATE(4, 29)
+NMF_HALS_INSTANTIATE(4, 19)
+NMF_HALS_INSTANTIATE(2, 22)
+NMF_HALS_INSTANTIATE(2, 12)
+NMF_HALS_INSTANTIATE(2, 6)

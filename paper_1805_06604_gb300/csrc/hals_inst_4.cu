@@ -1,10 +1,9 @@
 // hals_inst_4.cu -- explicit instantiations of the HALS sweep kernel
-// (hals_impl.cuh) for (lanes, slots) = (4, 20), (4, 13), (4, 10), (4, 8), (2, 8), (2, 2).
+// (hals_impl.cuh) for (lanes, slots) = (4, 28), (2, 30), (2, 23), (2, 13), (2, 8).
 #include "hals_impl.cuh"
 
-NMF_HALS_INSTANTIATE(4, 20)
-NMF_HALS_INSTANTIATE(4, 13)
-NMF_HALS_INSTANTIATE(4, 10)
-NMF_HALS_INSTANTIATE(4, 8)
+NMF_HALS_INSTANTIATE(4, 28)
+NMF_HALS_INSTANTIATE(2, 30)
+NMF_HALS_INSTANTIATE(2, 23)
+NMF_HALS_INSTANTIATE(2, 13)
 NMF_HALS_INSTANTIATE(2, 8)
-NMF_HALS_INSTANTIATE(2, 2)

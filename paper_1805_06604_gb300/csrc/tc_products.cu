@@ -5,19 +5,23 @@
 // K), N <= 128.  Used as C = X H_y^T (P = X, Q = H_y) and as A^T = X^T W_y
 // (P = X^T, a transposed copy of X kept for these modes, Q = W_y^T).
 //
-// Per CTA: one 128-row tile of P, all N columns, a range of K (split-K).
-// Tiles arrive by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a
-// 4-stage shared-memory ring; one thread issues tcgen05.mma into an FP32
-// accumulator in tensor memory; after the last K step the four warps read
-// their 32 TMEM lanes (tcgen05.ld) and write the tile.  Split partials are
-// summed in split order by the last CTA of a row tile (atomic ticket).
+// Persistent stream-K kernel: one CTA per SM, each owning an equal share of
+// the (128-row tile of P, 64-element K stage) units, so every SM streams the
+// same number of bytes of X.  A stage (two 128-byte-wide boxes of P and Q)
+// arrives by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a shared-
+// memory ring; one thread issues tcgen05.mma into an FP32 accumulator in
+// tensor memory, two of which alternate between the tiles a CTA touches;
+// four warps read a finished accumulator (tcgen05.ld) and write the tile, or
+// a partial of it that the tile's last CTA (atomic ticket) adds to the other
+// partials in CTA order -- deterministic.
 //
 //  TF32:     D += P Q^T with the operands read as TF32 (one product).
 //  BF16X3:   P and Q are held as hi/lo BF16 pairs (x ~ hi + lo); three
 //            products hi.hi + hi.lo + lo.hi accumulate in FP32.
 //
 // Every mbarrier wait is bounded; a wait that runs out sets *err_flag, the
-// CTA skips the rest of its work, frees its tensor memory and returns.
+// CTA skips the rest of its work, waits (bounded) for its copies and MMAs in
+// flight, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -28,7 +32,6 @@
 namespace nmfg {
 namespace {
 
-constexpr int kThreads = 128;
 constexpr int kBM = 128;
 constexpr int kAtom = 128;                      // bytes per swizzled row
 constexpr unsigned long long kSpinLimit = 1ull << 26;
@@ -66,12 +69,43 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
     return false;
 }
 
+// Bounded wait for a long phase (a whole accumulation): polls with a short
+// sleep so that the waiting thread takes no issue slots or barrier-unit
+// bandwidth from the producer and the MMA issuer.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity, int *err) {
+    const uint32_t a = smem_u32(bar);
+    for (unsigned long long i = 0; i < (kSpinLimit >> 2); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        __nanosleep(128);
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1,
                                             uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
         "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
         "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Contiguous global -> shared copy (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"((unsigned long long)src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -136,47 +170,84 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 template <int KIND, int N>
 struct TcCfg {
     static constexpr int kElem = KIND == 0 ? 4 : 2;            // bytes per element
-    static constexpr int kBK = kAtom / kElem;                  // K elements per stage
-    static constexpr int kPBytes = kBM * kAtom;                // one P tile
-    static constexpr int kQBytes = N * kAtom;                  // one Q tile
+    static constexpr int kAtomK = kAtom / kElem;               // K elements per 128-byte atom
+    static constexpr int kAtoms = KIND == 0 ? 2 : 1;           // K atoms per stage
     static constexpr int kParts = KIND == 0 ? 1 : 2;           // hi (and lo)
-    static constexpr int kStageBytes = kParts * (kPBytes + kQBytes);
-    static constexpr int kKSteps = kAtom / 32;                 // MMAs of 32 bytes of K
+    static constexpr int kBoxes = kAtoms * kParts;             // P boxes (and Q boxes) per stage
+    static constexpr int kBK = kAtoms * kAtomK;                // K elements per stage
+    static constexpr int kPBytes = kBM * kAtom;                // one P box
+    static constexpr int kQBytes = N * kAtom;                  // one Q box
+    static constexpr int kStageBytes = kBoxes * (kPBytes + kQBytes);
+    static constexpr int kKSteps = kAtom / 32;                 // MMAs per atom (32 bytes of K)
     static constexpr uint32_t kIdesc = instr_desc(KIND == 0 ? 2 : 1, kBM, N);
-    static constexpr int kTmemCols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
-    static constexpr int kStages = (4 * kStageBytes <= 200 * 1024) ? 4 : (200 * 1024) / kStageBytes;
+    static constexpr int kAccCols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);   // one accumulator
+    static constexpr int kTmemCols = 2 * kAccCols;             // double-buffered
+    static constexpr int kFit = (200 * 1024) / kStageBytes;
+    static constexpr int kStages = kFit < 2 ? 2 : (kFit > 6 ? 6 : kFit);
+    static_assert(kStages * kStageBytes + 2048 <= 227 * 1024, "stage ring exceeds shared memory");
 };
 
+constexpr int kTcThreads = 192;   // warps 0-3: epilogue, warp 4: TMA producer, warp 5: MMA issuer
+constexpr int kMaxContrib = 64;   // CTAs that may share one row tile
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void epilogue_sync() {
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// Stream-K schedule over the (row tile, K stage) units, tile-major: CTA c
+// owns units [total*c/G, total*(c+1)/G), so every CTA of a single wave gets
+// the same amount of X.  A CTA's range splits into segments, one per row
+// tile it touches.
+struct StreamK {
+    int64_t total, G;
+    int nk;
+    __device__ int64_t begin(int64_t c) const { return total * c / G; }
+    __device__ int64_t cta_of(int64_t u) const { return ((u + 1) * G - 1) / total; }
+};
+
+// out = P Q^T (see the top of the file).  Warp-specialised: warp 4 lane 0
+// streams stages of P and Q boxes by TMA into a ring; warp 5 lane 0 issues
+// tcgen05.mma into one of two TMEM accumulators (alternating per segment);
+// warps 0-3 drain a finished accumulator (tcgen05.ld, 32 rows each) and
+// write the tile, or a partial of it plus an ordered fix-up by the last of
+// the tile's CTAs.
 template <int KIND, int N, bool TRANS_OUT>
-__global__ void __launch_bounds__(kThreads, 1)
-tc_gemm_kernel(const __grid_constant__ CUtensorMap map_p, const __grid_constant__ CUtensorMap map_q,
-               const __grid_constant__ CUtensorMap map_p_lo,
-               const __grid_constant__ CUtensorMap map_q_lo, int64_t M, int64_t K, int nvalid,
-               float *__restrict__ out, int64_t out_ld, int64_t k_per_split,
-               float *__restrict__ part, unsigned int *__restrict__ tickets, int *err_flag) {
+__global__ void __launch_bounds__(kTcThreads, 1)
+tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__restrict__ pk_lo,
+               const __grid_constant__ CUtensorMap map_q,
+               const __grid_constant__ CUtensorMap map_q_lo, int64_t M, int64_t tiles, int nk,
+               int nvalid, float *__restrict__ out, int64_t out_ld, float *__restrict__ part,
+               int seg_max, unsigned int *__restrict__ tickets, int *err_flag) {
     using Cfg = TcCfg<KIND, N>;
+    constexpr int kStages = Cfg::kStages;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int kStages = Cfg::kStages;
-    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain_bar;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int skip_sh;
-    __shared__ bool am_last;
+    __shared__ int abort_sh, seg_ok_sh;
+    __shared__ bool am_last_sh;
+    __shared__ int64_t contrib_sh[kMaxContrib];
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t row0 = (int64_t)blockIdx.x * kBM;
-    const int split = blockIdx.y, nsplit = gridDim.y;
-    const int64_t kbeg = (int64_t)split * k_per_split;
-    const int64_t kend = min(K, kbeg + k_per_split);
-    const int nk = kend > kbeg ? (int)((kend - kbeg + Cfg::kBK - 1) / Cfg::kBK) : 0;
+    const StreamK sk{tiles * nk, (int64_t)gridDim.x, nk};
+    const int64_t u_begin = sk.begin(blockIdx.x), u_end = sk.begin(blockIdx.x + 1);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&done_bar, 1);
-        skip_sh = 0;
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
+        mbar_init(&drain_bar, 1);
+        abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -191,115 +262,228 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap map_p, const __grid_constant_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
 
-    if (threadIdx.x == 0 && nk > 0) {
-        // TMA producer.
-        for (int it = 0; it < nk; ++it) {
-            const int s = it % kStages;
-            if (it >= kStages && !mbar_wait(&empty_bar[s], ((it / kStages) - 1) & 1, err_flag)) {
-                skip_sh = 1;
-                break;
+    if (warp == 4) {
+        if (lane == 0) {
+            // TMA producer: every K stage of every segment, in order.
+            int it = 0;
+            bool ok = true;
+            for (int64_t u = u_begin; ok && u < u_end;) {
+                const int64_t tile = u / nk;
+                const int ks0 = (int)(u % nk);
+                const int ks1 = (int)min((int64_t)nk, ks0 + (u_end - u));
+                for (int ks = ks0; ks < ks1; ++ks, ++it) {
+                    const int s = it % kStages;
+                    if (it >= kStages &&
+                        !mbar_wait(&empty_bar[s], ((it / kStages) - 1) & 1, err_flag)) {
+                        abort_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *st = smem + s * Cfg::kStageBytes;
+                    unsigned char *qs = st + Cfg::kBoxes * Cfg::kPBytes;
+                    const int k0 = ks * Cfg::kBK;
+                    mbar_expect_tx(&full_bar[s], Cfg::kStageBytes);
+#pragma unroll
+                    for (int b = 0; b < Cfg::kBoxes; ++b) {
+                        // TF32: box b is K atom b.  BF16X3: box b is part b (hi, lo).
+                        // P comes from its packed copy: block (tile, atom) is one
+                        // contiguous, already swizzled 16 KiB image.
+                        const int kb = KIND == 0 ? k0 + b * Cfg::kAtomK : k0;
+                        const int64_t atom = (int64_t)ks * Cfg::kAtoms + (KIND == 0 ? b : 0);
+                        const unsigned char *src = ((KIND == 1 && b == 1) ? pk_lo : pk) +
+                                                   (tile * ((int64_t)nk * Cfg::kAtoms) + atom) *
+                                                       Cfg::kPBytes;
+                        const CUtensorMap *mq = (KIND == 1 && b == 1) ? &map_q_lo : &map_q;
+                        bulk_load(st + b * Cfg::kPBytes, src, Cfg::kPBytes, &full_bar[s]);
+                        tma_load_2d(qs + b * Cfg::kQBytes, mq, kb, 0, &full_bar[s]);
+                    }
+                }
+                u += ks1 - ks0;
             }
-            unsigned char *st = smem + s * Cfg::kStageBytes;
-            const int k0 = (int)(kbeg + (int64_t)it * Cfg::kBK);
-            mbar_expect_tx(&full_bar[s], Cfg::kStageBytes);
-            tma_load_2d(st, &map_p, k0, (int)row0, &full_bar[s]);
-            tma_load_2d(st + Cfg::kPBytes, &map_q, k0, 0, &full_bar[s]);
-            if constexpr (KIND == 1) {
-                tma_load_2d(st + Cfg::kPBytes + Cfg::kQBytes, &map_p_lo, k0, (int)row0,
-                            &full_bar[s]);
-                tma_load_2d(st + 2 * Cfg::kPBytes + Cfg::kQBytes, &map_q_lo, k0, 0,
-                            &full_bar[s]);
-            }
+            // Copies still in flight (after an abort) land before the CTA exits.
+            for (int j = it - kStages < 0 ? 0 : it - kStages; j < it; ++j)
+                mbar_wait(&full_bar[j % kStages], (j / kStages) & 1, err_flag);
         }
-    } else if (threadIdx.x == 32 && nk > 0) {
-        // MMA issuer.
-        for (int it = 0; it < nk; ++it) {
-            const int s = it % kStages;
-            if (!mbar_wait(&full_bar[s], (it / kStages) & 1, err_flag)) {
-                skip_sh = 1;
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer.
+            int it = 0, seg = 0;
+            bool ok = true;
+            for (int64_t u = u_begin; ok && u < u_end; ++seg) {
+                const int ks0 = (int)(u % nk);
+                const int ks1 = (int)min((int64_t)nk, ks0 + (u_end - u));
+                const int b = seg & 1;
+                if (seg >= 2 && !mbar_wait(&acc_empty[b], ((seg >> 1) - 1) & 1, err_flag)) {
+                    abort_sh = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(b * Cfg::kAccCols);
+                for (int ks = ks0; ks < ks1; ++ks, ++it) {
+                    const int s = it % kStages;
+                    if (!mbar_wait(&full_bar[s], (it / kStages) & 1, err_flag)) {
+                        abort_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t base = smem_u32(smem + s * Cfg::kStageBytes);
+                    const uint32_t qbase = base + Cfg::kBoxes * Cfg::kPBytes;
+#pragma unroll
+                    for (int a = 0; a < Cfg::kAtoms; ++a) {
+#pragma unroll
+                        for (int kk = 0; kk < Cfg::kKSteps; ++kk) {
+                            const uint32_t off = kk * 32;
+                            const uint32_t acc = (ks > ks0 || a > 0 || kk > 0) ? 1u : 0u;
+                            const uint32_t ph = base + a * Cfg::kPBytes + off;
+                            const uint32_t qh = qbase + a * Cfg::kQBytes + off;
+                            mma<KIND>(d, smem_desc(ph), smem_desc(qh), Cfg::kIdesc, acc);
+                            if constexpr (KIND == 1) {
+                                const uint32_t pl = base + Cfg::kPBytes + off;
+                                const uint32_t ql = qbase + Cfg::kQBytes + off;
+                                mma<KIND>(d, smem_desc(ph), smem_desc(ql), Cfg::kIdesc, 1u);
+                                mma<KIND>(d, smem_desc(pl), smem_desc(qh), Cfg::kIdesc, 1u);
+                            }
+                        }
+                    }
+                    mma_commit(&empty_bar[s]);
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[b]);
+                u += ks1 - ks0;
+            }
+            // Every MMA issued so far has completed before TMEM is freed.
+            mma_commit(&drain_bar);
+            mbar_wait(&drain_bar, 0, err_flag);
+        }
+    } else {
+        // Epilogue warps 0-3: warp w owns TMEM lanes (tile rows) 32w .. 32w+31.
+        int seg = 0;
+        for (int64_t u = u_begin; u < u_end; ++seg) {
+            const int64_t tile = u / nk;
+            const int ks0 = (int)(u % nk);
+            const int ks1 = (int)min((int64_t)nk, ks0 + (u_end - u));
+            u += ks1 - ks0;
+            const int b = seg & 1;
+            // The waiting thread sits in warp 2, a scheduler that neither the
+            // producer (warp 4) nor the MMA issuer (warp 5) uses.
+            if (threadIdx.x == 64) seg_ok_sh = mbar_wait_sleep(&acc_full[b], (seg >> 1) & 1, err_flag);
+            epilogue_sync();
+            const int seg_ok = seg_ok_sh;
+            epilogue_sync();            // all four warps read the flag before it is rewritten
+            if (!seg_ok) {
+                abort_sh = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = smem_u32(smem + s * Cfg::kStageBytes);
-            const uint32_t p_hi = base, q_hi = base + Cfg::kPBytes;
+            float v[N];
 #pragma unroll
-            for (int ks = 0; ks < Cfg::kKSteps; ++ks) {
-                const uint32_t off = ks * 32;
-                const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
-                mma<KIND>(tmem, smem_desc(p_hi + off), smem_desc(q_hi + off), Cfg::kIdesc, acc);
-                if constexpr (KIND == 1) {
-                    const uint32_t p_lo = base + Cfg::kPBytes + Cfg::kQBytes;
-                    const uint32_t q_lo = p_lo + Cfg::kPBytes;
-                    mma<KIND>(tmem, smem_desc(p_hi + off), smem_desc(q_lo + off), Cfg::kIdesc, 1u);
-                    mma<KIND>(tmem, smem_desc(p_lo + off), smem_desc(q_hi + off), Cfg::kIdesc, 1u);
-                }
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float w16[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * Cfg::kAccCols + c0),
+                          w16);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[c0 + i] = w16[i];
             }
-            mma_commit(&empty_bar[s]);
-        }
-        mma_commit(&done_bar);
-    }
-    __syncthreads();
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
 
-    // Epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31.
-    float *my_part = nullptr;
-    const bool have_result = nk > 0 && !skip_sh && mbar_wait(&done_bar, 0, err_flag);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int64_t row = row0 + warp * 32 + lane;
-    if (nsplit > 1) my_part = part + ((int64_t)blockIdx.x * nsplit + split) * (kBM * N);
+            const int64_t row0 = tile * kBM;
+            const int64_t row = row0 + warp * 32 + lane;
+            const int64_t first = sk.cta_of(tile * nk), last = sk.cta_of((tile + 1) * nk - 1);
+            if (first == last) {
+                // The whole K range of the tile: write it.
+                if (row < M) {
 #pragma unroll
-    for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
-        if (have_result) {
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        } else {
+                    for (int col = 0; col < N; ++col) {
+                        if (col < nvalid) {
+                            if (TRANS_OUT) out[(int64_t)col * out_ld + row] = v[col];
+                            else out[row * out_ld + col] = v[col];
+                        }
+                    }
+                }
+                continue;
+            }
+            // Partial of a shared tile: slot (CTA, its segment index).
+            const int64_t slot = (int64_t)blockIdx.x * seg_max + seg;
+            float *dst = part + (slot * kBM + warp * 32 + lane) * N;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0.0f;
-        }
-        if (nsplit > 1) {
-            float *dst = my_part + (int64_t)(warp * 32 + lane) * N + c0;
+            for (int i = 0; i < N; i += 4)
+                *reinterpret_cast<float4 *>(dst + i) =
+                    make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            __threadfence();
+            epilogue_sync();
+            if (threadIdx.x == 0) {
+                const unsigned int t = atomicAdd(tickets + tile, 1u);
+                am_last_sh = (t == (unsigned)(last - first));
+            }
+            epilogue_sync();
+            if (!am_last_sh) continue;
+            // Last CTA of the tile: add the other contributors' partials to
+            // the own rows still in registers, in CTA order (each thread its
+            // row, every load in flight at once), and write the tile.
+            __threadfence();
+            const int nc = (int)(last - first + 1);
+            if (threadIdx.x < nc && threadIdx.x < kMaxContrib) {
+                const int64_t c = first + threadIdx.x;
+                contrib_sh[threadIdx.x] = (c * seg_max + (tile - sk.begin(c) / nk)) * (kBM * N);
+            }
+            epilogue_sync();
+            if (nc > kMaxContrib) {
+                if (threadIdx.x == 0) atomicExch(err_flag, 2);
+            } else {
+                // Column blocks of 16 keep the register footprint small; the
+                // sum runs in CTA order whichever CTA is last (deterministic).
+                const float *myrow = part + (int64_t)(warp * 32 + lane) * N;
 #pragma unroll
-            for (int i = 0; i < 16; i += 4)
-                *reinterpret_cast<float4 *>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-        } else if (row < M) {
+                for (int cb = 0; cb < N; cb += 16) {
+                    float sum[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int col = c0 + i;
-                if (col < nvalid) {
-                    if (TRANS_OUT) out[(int64_t)col * out_ld + row] = v[i];
-                    else out[row * out_ld + col] = v[i];
+                    for (int i = 0; i < 16; ++i) sum[i] = 0.0f;
+                    for (int j = 0; j < nc; ++j) {
+                        if (first + j == (int64_t)blockIdx.x) {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) sum[i] += v[cb + i];
+                        } else {
+                            const float4 *src =
+                                reinterpret_cast<const float4 *>(myrow + contrib_sh[j] + cb);
+                            float4 w[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) w[i] = __ldcg(src + i);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                sum[4 * i] += w[i].x;
+                                sum[4 * i + 1] += w[i].y;
+                                sum[4 * i + 2] += w[i].z;
+                                sum[4 * i + 3] += w[i].w;
+                            }
+                        }
+                    }
+                    if (row < M) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int col = cb + i;
+                            if (col < nvalid) {
+                                if (TRANS_OUT) out[(int64_t)col * out_ld + row] = sum[i];
+                                else out[row * out_ld + col] = sum[i];
+                            }
+                        }
+                    }
                 }
             }
+            if (threadIdx.x == 0) tickets[tile] = 0u;
         }
     }
+
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(Cfg::kTmemCols)
                      : "memory");
-    if (nsplit == 1) return;
-
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned int t = atomicAdd(tickets + blockIdx.x, 1u);
-        am_last = (t == (unsigned)nsplit - 1);
     }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
-    const float *base = part + (int64_t)blockIdx.x * nsplit * (kBM * N);
-    for (int e = threadIdx.x; e < kBM * N; e += kThreads) {
-        float s = 0.0f;
-        for (int q = 0; q < nsplit; ++q) s += __ldcg(base + (int64_t)q * kBM * N + e);
-        const int64_t r_ = row0 + e / N;
-        const int col = e % N;
-        if (r_ < M && col < nvalid) {
-            if (TRANS_OUT) out[(int64_t)col * out_ld + r_] = s;
-            else out[r_ * out_ld + col] = s;
-        }
-    }
-    if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;
 }
 
 // ------------------------------------------------------------ host side
@@ -335,20 +519,24 @@ bool make_map(CUtensorMap *map, const void *ptr, bool bf16, int64_t rows, int64_
 }
 
 struct TcPlan {
-    int nsplit;
-    int64_t tiles, k_per_split;
+    int64_t tiles;
+    int nk, grid, seg_max;
 };
 
-TcPlan plan_tc(int64_t M, int64_t K, int bk) {
+// One persistent CTA per SM (the stage ring fills most of its shared
+// memory), each with an equal share of the (row tile, K stage) units.
+template <int KIND, int N>
+TcPlan plan_for(int64_t M, int64_t K) {
+    using Cfg = TcCfg<KIND, N>;
     TcPlan p;
     p.tiles = (M + kBM - 1) / kBM;
-    int64_t want = (kNumSMs + p.tiles - 1) / p.tiles;               // ~1 CTA per SM
-    const int64_t max_split = (K + 8 * bk - 1) / (8 * bk);
-    if (want > max_split) want = max_split;
-    if (want < 1) want = 1;
-    if (want > 16) want = 16;
-    p.k_per_split = ((K + want - 1) / want + bk - 1) / bk * bk;
-    p.nsplit = (int)((K + p.k_per_split - 1) / p.k_per_split);
+    p.nk = (int)((K + Cfg::kBK - 1) / Cfg::kBK);
+    const int64_t total = p.tiles * p.nk;
+    p.grid = (int)(total < kNumSMs ? total : kNumSMs);
+    // At most 32 CTAs per row tile keeps a tile's contributors <= 34 < kMaxContrib.
+    if (p.grid > p.tiles * 32) p.grid = (int)(p.tiles * 32);
+    const int64_t per = p.grid > 0 ? (total + p.grid - 1) / p.grid : 0;
+    p.seg_max = p.nk > 0 ? (int)((per + p.nk - 1) / p.nk + 1) : 1;
     return p;
 }
 
@@ -356,19 +544,15 @@ template <int KIND, int N, bool TRANS>
 cudaError_t tc_launch(const TcOperands &o, float *out, int64_t out_ld, void *ws,
                       unsigned int *tickets, int *err_flag, cudaStream_t st) {
     using Cfg = TcCfg<KIND, N>;
-    const TcPlan p = plan_tc(o.M, o.K, Cfg::kBK);
-    CUtensorMap mp, mq, mpl, mql;
+    const TcPlan p = plan_for<KIND, N>(o.M, o.K);
+    if (p.grid < 1) return cudaErrorInvalidValue;
+    CUtensorMap mq, mql;
     const bool bf = KIND == 1;
     // Q has q_rows <= N real rows; the N-row box reads zeros beyond them.
-    if (!make_map(&mp, o.P, bf, o.M, o.K, o.ldp, kBM) ||
-        !make_map(&mq, o.Q, bf, o.q_rows, o.K, o.ldq, N))
-        return cudaErrorInvalidValue;
+    if (!make_map(&mq, o.Q, bf, o.q_rows, o.K, o.ldq, N)) return cudaErrorInvalidValue;
     if (bf) {
-        if (!make_map(&mpl, o.P_lo, bf, o.M, o.K, o.ldp, kBM) ||
-            !make_map(&mql, o.Q_lo, bf, o.q_rows, o.K, o.ldq, N))
-            return cudaErrorInvalidValue;
+        if (!make_map(&mql, o.Q_lo, bf, o.q_rows, o.K, o.ldq, N)) return cudaErrorInvalidValue;
     } else {
-        mpl = mp;
         mql = mq;
     }
     const size_t smem = (size_t)Cfg::kStages * Cfg::kStageBytes + 1024;
@@ -376,10 +560,11 @@ cudaError_t tc_launch(const TcOperands &o, float *out, int64_t out_ld, void *ws,
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)p.tiles, (unsigned)p.nsplit);
-    kern<<<grid, kThreads, smem, st>>>(mp, mq, mpl, mql, o.M, o.K, o.nvalid, out, out_ld,
-                                       p.k_per_split, static_cast<float *>(ws), tickets,
-                                       err_flag);
+    kern<<<p.grid, kTcThreads, smem, st>>>(static_cast<const unsigned char *>(o.P),
+                                           static_cast<const unsigned char *>(o.P_lo), mq, mql,
+                                           o.M, p.tiles, p.nk, o.nvalid, out,
+                                           out_ld, static_cast<float *>(ws), p.seg_max, tickets,
+                                           err_flag);
     return cudaGetLastError();
 }
 
@@ -396,6 +581,60 @@ cudaError_t tc_dispatch_n(const TcOperands &o, float *out, int64_t out_ld, void 
         case 112: return tc_launch<KIND, 112, TRANS>(o, out, out_ld, ws, tickets, err_flag, st);
         case 128: return tc_launch<KIND, 128, TRANS>(o, out, out_ld, ws, tickets, err_flag, st);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+// Packed P: for every 128-row tile t and 128-byte K atom a, one 16 KiB block
+// at ((t * atoms + a) * 16 KiB) that is the exact shared-memory image a TMA
+// load with 128-byte swizzle would produce: row i at i * 128 bytes, its
+// 16-byte chunk c at chunk position c ^ (i % 8).  Rows >= M and K >= K are
+// zero.  `atoms` is the number of atoms per tile, a whole number of stages.
+// TF32: 32 fp32 per atom row.  BF16X3: 64 bf16 per atom row, in a hi and a
+// lo array (x ~ hi + lo).
+template <bool TRANS, bool BF>
+__global__ void __launch_bounds__(256)
+pack_kernel(const float *__restrict__ x, int64_t rows, int64_t cols, int64_t ld, int64_t atoms,
+            unsigned char *__restrict__ out_hi, unsigned char *__restrict__ out_lo) {
+    // P = x (TRANS false: M = rows, K = cols) or P = x^T (M = cols, K = rows).
+    constexpr int kAtomK = BF ? 64 : 32;
+    const int64_t M = TRANS ? cols : rows, K = TRANS ? rows : cols;
+    const int64_t t = blockIdx.y, a = blockIdx.x;
+    __shared__ float tile[TRANS ? kAtomK : 1][TRANS ? 129 : 1];
+    if constexpr (TRANS) {
+        // Stage x[a*kAtomK .. +kAtomK][t*128 .. +128] (coalesced along columns).
+        for (int e = threadIdx.x; e < kAtomK * 128; e += 256) {
+            const int kr = e / 128, ci = e % 128;
+            const int64_t gr = a * kAtomK + kr, gc = t * 128 + ci;
+            tile[kr][ci] = (gr < rows && gc < cols) ? x[gr * ld + gc] : 0.0f;
+        }
+        __syncthreads();
+    }
+    unsigned char *blk_hi = out_hi + (t * atoms + a) * 16384;
+    unsigned char *blk_lo = BF ? out_lo + (t * atoms + a) * 16384 : nullptr;
+    constexpr int kPer = BF ? 8 : 4;                 // elements per 16-byte chunk
+    for (int e = threadIdx.x; e < 128 * 8; e += 256) {
+        const int i = e / 8, c = e % 8;              // P row in the tile, chunk
+        const int64_t prow = t * 128 + i;
+        float v[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int64_t k = a * kAtomK + c * kPer + j;
+            if constexpr (TRANS) v[j] = tile[c * kPer + j][i];
+            else v[j] = (prow < M && k < K) ? x[prow * ld + k] : 0.0f;
+        }
+        const int pos = i * 128 + ((c ^ (i & 7)) << 4);
+        if constexpr (BF) {
+            __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                h[j] = __float2bfloat16_rn(v[j]);
+                l[j] = __float2bfloat16_rn(v[j] - __bfloat162float(h[j]));
+            }
+            *reinterpret_cast<uint4 *>(blk_hi + pos) = *reinterpret_cast<const uint4 *>(h);
+            *reinterpret_cast<uint4 *>(blk_lo + pos) = *reinterpret_cast<const uint4 *>(l);
+        } else {
+            *reinterpret_cast<float4 *>(blk_hi + pos) = make_float4(v[0], v[1], v[2], v[3]);
+        }
     }
 }
 
@@ -432,13 +671,59 @@ __global__ void transpose_kernel(const float *__restrict__ in, int64_t rows, int
 
 }  // namespace
 
+template <int KIND>
+TcPlan plan_dispatch(int64_t M, int64_t K, int N) {
+    switch (N) {
+        case 16: return plan_for<KIND, 16>(M, K);
+        case 32: return plan_for<KIND, 32>(M, K);
+        case 48: return plan_for<KIND, 48>(M, K);
+        case 64: return plan_for<KIND, 64>(M, K);
+        case 80: return plan_for<KIND, 80>(M, K);
+        case 96: return plan_for<KIND, 96>(M, K);
+        case 112: return plan_for<KIND, 112>(M, K);
+        default: return plan_for<KIND, 128>(M, K);
+    }
+}
+
 size_t tc_ws_bytes(int64_t M, int64_t K, int N, int precision) {
-    const TcPlan p = plan_tc(M, K, precision == NMF_PREC_TF32 ? 32 : 64);
-    if (p.nsplit == 1) return 256;
-    return sizeof(float) * (size_t)p.tiles * p.nsplit * kBM * N;
+    const TcPlan p = precision == NMF_PREC_TF32 ? plan_dispatch<0>(M, K, N)
+                                                : plan_dispatch<1>(M, K, N);
+    return sizeof(float) * (size_t)(p.grid > 0 ? p.grid : 1) * p.seg_max * kBM * N;
 }
 
 int64_t tc_num_tickets(int64_t M) { return (M + kBM - 1) / kBM; }
+
+// Atoms per tile of the packed P: K rounded up to whole stages.
+int64_t tc_packed_atoms(int64_t K, int precision) {
+    const int bk = 64;                               // K elements per stage, both precisions
+    const int atoms_per_stage = precision == NMF_PREC_TF32 ? 2 : 1;
+    return (K + bk - 1) / bk * atoms_per_stage;
+}
+
+size_t tc_packed_bytes(int64_t M, int64_t K, int precision) {
+    return (size_t)((M + kBM - 1) / kBM) * (size_t)tc_packed_atoms(K, precision) * 16384;
+}
+
+cudaError_t launch_tc_pack(const float *x, int64_t rows, int64_t cols, int64_t ld, bool transposed,
+                           int precision, void *out_hi, void *out_lo, cudaStream_t st) {
+    const int64_t M = transposed ? cols : rows, K = transposed ? rows : cols;
+    const int64_t atoms = tc_packed_atoms(K, precision);
+    const int64_t tiles = (M + kBM - 1) / kBM;
+    if (tiles > 65535 || atoms > 0x7fffffff) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)atoms, (unsigned)tiles);
+    auto *hi = static_cast<unsigned char *>(out_hi);
+    auto *lo = static_cast<unsigned char *>(out_lo);
+    if (precision == NMF_PREC_TF32) {
+        if (transposed) pack_kernel<true, false><<<grid, 256, 0, st>>>(x, rows, cols, ld, atoms, hi, lo);
+        else pack_kernel<false, false><<<grid, 256, 0, st>>>(x, rows, cols, ld, atoms, hi, lo);
+    } else if (precision == NMF_PREC_BF16X3) {
+        if (transposed) pack_kernel<true, true><<<grid, 256, 0, st>>>(x, rows, cols, ld, atoms, hi, lo);
+        else pack_kernel<false, true><<<grid, 256, 0, st>>>(x, rows, cols, ld, atoms, hi, lo);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 bool tc_available() { return encode_fn() != nullptr; }
 

@@ -59,6 +59,7 @@ def _check_step(res):
     (200, 150, 10, 1, 6),      # hp = 1 (H extrapolated after the W-update)
     (130, 77, 1, 3, 3),        # r = 1
     (150, 140, 128, 3, 2),     # r at the build cap
+    (400, 300, 90, 3, 3),      # four lanes per item, r not a multiple of 4
 ])
 def test_single_step_matches_oracle(m, n, r, hp, warm):
     P = wl.low_rank(m, n, r, seed=m + n + r, noise=0.02)
