@@ -161,6 +161,21 @@ def load_traffic(kernel: str):
     return ent.get("bytes_per_launch")
 
 
+def direct_relerr(Xd, W, H):
+    """||X - W H||_F / ||X||_F of returned factors, evaluated directly in FP64
+    on the device in row blocks (a check beside the solver's own e(k))."""
+    import torch
+    Wd = torch.as_tensor(W, device=Xd.device, dtype=torch.float64)
+    Hd = torch.as_tensor(H, device=Xd.device, dtype=torch.float64)
+    num = 0.0
+    den = 0.0
+    for i in range(0, Xd.shape[0], 1024):
+        Xb = Xd[i:i + 1024].double()
+        num += float(((Xb - Wd[i:i + 1024] @ Hd) ** 2).sum())
+        den += float((Xb ** 2).sum())
+    return (num / den) ** 0.5
+
+
 def cpu_baseline_oracle(P, lw, lh, iters: int):
     import numpy as np
     import oracle as O
@@ -324,6 +339,35 @@ def run_ours(args, world, rank, local):
     line["iteration_roofline"] = {"bound_us": bound_s * 1e6, "frac": bound_s / (t / args.steps),
                                   "x_bytes": it_bytes, "flops": it_flops}
     line["phases"] = phases
+
+    # The tensor-core precision modes on the same workload (X products on
+    # tcgen05 from a packed copy of X): iteration rate, the X products
+    # against HBM, and the relative error beside the FP32 run's.
+    modes = {}
+    Wf, Hf = solver.factors()
+    fp32_direct = direct_relerr(Xd, Wf, Hf)
+    line["relerr_direct"] = fp32_direct
+    for name, prec in (("tf32", nmf.NMF_PREC_TF32), ("bf16x3", nmf.NMF_PREC_BF16X3)):
+        sv = nmf.Solver(Xd, P.r, W0d, H0d, stream=stream, precision=prec)
+        sv.step(args.warmup)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sv.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tm = e0.elapsed_time(e1) / 1000.0
+        pm = sv.profile_phases(prof_iters)
+        Wm, Hm = sv.factors()
+        modes[name] = {
+            "iters_per_s": args.steps / tm, "ms_per_step": 1000.0 * tm / args.steps,
+            "relerr_direct": direct_relerr(Xd, Wm, Hm), "fp32_relerr_direct": fp32_direct,
+            "relerr_from_e_k": sv.info().relerr,
+            "x_products_hbm": {k: {"us": 1000.0 * pm[k],
+                                   "gbs": xbytes[k] / (pm[k] / 1000.0) / 1e9,
+                                   "frac_of_hbm": xbytes[k] / (pm[k] / 1000.0) / 1e9 / hbm_gbs}
+                               for k in xbytes}}
+        sv.close()
+    line["precision_modes"] = modes
 
     # End to end through the public API from pinned host buffers: create
     # (X, W0, H0 uploaded), `steps` iterations, factors read back.

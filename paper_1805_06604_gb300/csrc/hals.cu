@@ -7,7 +7,7 @@ namespace nmfg {
 template <int T, int S, int LAYOUT>
 cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const float *G, int rs,
                         const float *Xin, float *Xout, int sweeps, const HEpilogue &hep,
-                        const WEpilogue &wep, cudaStream_t st);
+                        const WEpilogue &wep, int cta_threads, cudaStream_t st);
 
 namespace {
 
@@ -16,7 +16,17 @@ namespace {
 constexpr int kSlots4[] = {17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32};
 constexpr int kSlots2[] = {2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 15, 16, 17,
                            18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32};
-constexpr int kThreadsPerCta = 128;
+// Threads per CTA of a sweep launch.  128 (one warp per scheduler of an
+// SM) unless the warps number between one and two per scheduler of the GPU:
+// there 128-thread CTAs leave a few SMs with twice the work of the rest,
+// and 64-thread CTAs spread it more evenly (dense 10000 x 4000 r = 50,
+// W side: 180 us against 200 us; the H side and the small and sparse
+// problems measured best at 128).
+int cta_threads(int64_t items, int T) {
+    const int64_t warps = (items * T + 31) / 32;
+    const int64_t schedulers = 4LL * kNumSMs;
+    return (warps > schedulers && warps <= 2 * schedulers) ? 64 : 128;
+}
 
 template <int N>
 int pick(const int (&list)[N], int need) {
@@ -41,7 +51,7 @@ cudaError_t dispatch(int64_t items, int r, int64_t ld, const float *A, const flo
 #define NMF_HALS_CASE(TV, SV)                                                                \
     case SV:                                                                                 \
         return hals_launch<TV, SV, LAYOUT>(items, r, ld, A, G, rs, Xin, Xout, sweeps, hep, wep, \
-                                           st);
+                                           cta_threads(items, T), st);
     if (T == 2) {
         switch (pick(kSlots2, need)) {
             NMF_HALS_CASE(2, 2) NMF_HALS_CASE(2, 3) NMF_HALS_CASE(2, 4) NMF_HALS_CASE(2, 5)
@@ -71,7 +81,7 @@ cudaError_t dispatch(int64_t items, int r, int64_t ld, const float *A, const flo
 
 int hals_w_num_ctas(int64_t m, int r) {
     const int T = pick_lanes(r);
-    const int64_t per_cta = kThreadsPerCta / T;
+    const int64_t per_cta = cta_threads(m, T) / T;
     return (int)((m + per_cta - 1) / per_cta);
 }
 

@@ -40,7 +40,7 @@
 namespace nmfg {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 128;                    // largest CTA (launches use 32..128)
 
 // Layout of one item's coordinates in global memory.
 //   kColumn: element k of item j at base[k * ld + j]   (columns of H)
@@ -212,7 +212,7 @@ hals_kernel(int64_t items, int r, int64_t ld,
     __syncthreads();
 
     const int t = threadIdx.x % T;
-    const int64_t item = (int64_t)blockIdx.x * (kThreads / T) + threadIdx.x / T;
+    const int64_t item = (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T;
     const bool valid = item < items;
     const unsigned gmask = 0xffffffffu;
 
@@ -414,7 +414,7 @@ hals_kernel(int64_t items, int r, int64_t ld,
         __syncthreads();
         if (threadIdx.x == 0) {
             double c = 0.0, qd = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) {
+            for (int w = 0; w < (int)blockDim.x / 32; ++w) {
                 c += red_cross[w];
                 qd += red_quad[w];
             }
@@ -443,7 +443,7 @@ hals_kernel(int64_t items, int r, int64_t ld,
             __syncthreads();
             if (threadIdx.x == 0) {
                 double cs = 0.0, qs = 0.0;
-                for (int w = 0; w < kThreads / 32; ++w) {
+                for (int w = 0; w < (int)blockDim.x / 32; ++w) {
                     cs += red_cross[w];
                     qs += red_quad[w];
                 }
@@ -462,7 +462,7 @@ hals_kernel(int64_t items, int r, int64_t ld,
 template <int T, int S, int LAYOUT>
 cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const float *G, int rs,
                         const float *Xin, float *Xout, int sweeps, const HEpilogue &hep,
-                        const WEpilogue &wep, cudaStream_t st) {
+                        const WEpilogue &wep, int cta_threads, cudaStream_t st) {
     constexpr int RP = S * T;
     constexpr int SP = 4 * ((S + 3) / 4) + (((S + 3) / 4) % 2 == 0 ? 4 : 0);
     const size_t smem = sizeof(float) * (size_t)(RP * T * SP * (LAYOUT == 1 ? 2 : 1) + RP * 16);
@@ -472,10 +472,11 @@ cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const 
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int64_t per_cta = kThreads / T;
+    if (cta_threads < 32 || cta_threads > kThreads || cta_threads % 32) return cudaErrorInvalidValue;
+    const int64_t per_cta = cta_threads / T;
     const unsigned grid = (unsigned)((items + per_cta - 1) / per_cta);
     if (grid == 0) return cudaSuccess;
-    kern<<<grid, kThreads, smem, st>>>(items, r, ld, A, G, rs, Xin, Xout, sweeps, 0, hep, wep);
+    kern<<<grid, cta_threads, smem, st>>>(items, r, ld, A, G, rs, Xin, Xout, sweeps, 0, hep, wep);
     return cudaGetLastError();
 }
 
@@ -484,6 +485,6 @@ cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const 
 #define NMF_HALS_INSTANTIATE_ONE(TV, SV, LV)                                                    \
     template cudaError_t nmfg::hals_launch<TV, SV, LV>(                                         \
         int64_t, int, int64_t, const float *, const float *, int, const float *, float *, int,  \
-        const nmfg::HEpilogue &, const nmfg::WEpilogue &, cudaStream_t);
+        const nmfg::HEpilogue &, const nmfg::WEpilogue &, int, cudaStream_t);
 // Both sides.
 #define NMF_HALS_INSTANTIATE(TV, SV) NMF_HALS_INSTANTIATE_ONE(TV, SV, 0) NMF_HALS_INSTANTIATE_ONE(TV, SV, 1)
