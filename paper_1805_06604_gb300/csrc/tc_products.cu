@@ -198,6 +198,33 @@ __device__ __forceinline__ void epilogue_sync() {
     asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
+// Writes columns c0 .. c0+CW-1 of one output row (values v[0..CW)):
+// transposed (column-major, coalesced across the warp's rows) or row-major,
+// as float4 words when `vec` (row stride and valid width multiples of 4).
+template <int CW, bool TRANS_OUT>
+__device__ __forceinline__ void store_row(const float (&v)[CW], int c0, int N, float *out,
+                                          int64_t out_ld, int64_t row, int64_t M, int nvalid,
+                                          bool vec) {
+    (void)N;
+    if (row >= M) return;
+    if (!TRANS_OUT && vec) {
+#pragma unroll
+        for (int i = 0; i < CW; i += 4)
+            if (c0 + i < nvalid)
+                *reinterpret_cast<float4 *>(out + row * out_ld + c0 + i) =
+                    make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < CW; ++i) {
+        const int col = c0 + i;
+        if (col < nvalid) {
+            if (TRANS_OUT) out[(int64_t)col * out_ld + row] = v[i];
+            else out[row * out_ld + col] = v[i];
+        }
+    }
+}
+
 // Stream-K schedule over the (row tile, K stage) units, tile-major: CTA c
 // owns units [total*c/G, total*(c+1)/G), so every CTA of a single wave gets
 // the same amount of X.  A CTA's range splits into segments, one per row
@@ -207,6 +234,34 @@ struct StreamK {
     int nk;
     __device__ int64_t begin(int64_t c) const { return total * c / G; }
     __device__ int64_t cta_of(int64_t u) const { return ((u + 1) * G - 1) / total; }
+};
+
+// The segments of one CTA's unit range [u0, u1) (one per row tile touched),
+// in processing order: the shorter of the two end segments first, then the
+// other, then the whole tiles between them.  End segments share their tile
+// with other CTAs, so their epilogues (a partial, or the fix-up) run while
+// later segments still stream; the last segment processed is, where there
+// is one, a whole tile (a plain store).  `orig` is the segment's index in
+// unit order, which names its partial slot.
+struct SegList {
+    int64_t u0, u1, t0;
+    int n, nk;
+    __device__ SegList(int64_t a, int64_t b, int k) : u0(a), u1(b), nk(k) {
+        t0 = a / k;
+        n = b > a ? (int)((b - 1) / k - t0 + 1) : 0;
+    }
+    __device__ void get(int p, int64_t &tile, int &ks0, int &ks1, int &orig) const {
+        if (n == 1) {
+            orig = 0;
+        } else {
+            const int64_t len_first = nk - u0 % nk, len_last = (u1 - 1) % nk + 1;
+            const bool first_short = len_first <= len_last;
+            orig = p == 0 ? (first_short ? 0 : n - 1) : p == 1 ? (first_short ? n - 1 : 0) : p - 1;
+        }
+        tile = t0 + orig;
+        ks0 = orig == 0 ? (int)(u0 % nk) : 0;
+        ks1 = orig == n - 1 ? (int)((u1 - 1) % nk + 1) : nk;
+    }
 };
 
 // out = P Q^T (see the top of the file).  Warp-specialised: warp 4 lane 0
@@ -235,7 +290,10 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const StreamK sk{tiles * nk, (int64_t)gridDim.x, nk};
-    const int64_t u_begin = sk.begin(blockIdx.x), u_end = sk.begin(blockIdx.x + 1);
+    // Row-major output rows can be written as float4 words when aligned.
+    const bool vec_out = !TRANS_OUT && out_ld % 4 == 0 && nvalid % 4 == 0 &&
+                         ((uintptr_t)out & 15) == 0;
+    const SegList segs(sk.begin(blockIdx.x), sk.begin(blockIdx.x + 1), nk);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -267,10 +325,10 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
             // TMA producer: every K stage of every segment, in order.
             int it = 0;
             bool ok = true;
-            for (int64_t u = u_begin; ok && u < u_end;) {
-                const int64_t tile = u / nk;
-                const int ks0 = (int)(u % nk);
-                const int ks1 = (int)min((int64_t)nk, ks0 + (u_end - u));
+            for (int sp = 0; ok && sp < segs.n; ++sp) {
+                int64_t tile;
+                int ks0, ks1, orig;
+                segs.get(sp, tile, ks0, ks1, orig);
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
                     const int s = it % kStages;
                     if (it >= kStages &&
@@ -298,7 +356,6 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                         tma_load_2d(qs + b * Cfg::kQBytes, mq, kb, 0, &full_bar[s]);
                     }
                 }
-                u += ks1 - ks0;
             }
             // Copies still in flight (after an abort) land before the CTA exits.
             for (int j = it - kStages < 0 ? 0 : it - kStages; j < it; ++j)
@@ -309,9 +366,10 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
             // MMA issuer.
             int it = 0, seg = 0;
             bool ok = true;
-            for (int64_t u = u_begin; ok && u < u_end; ++seg) {
-                const int ks0 = (int)(u % nk);
-                const int ks1 = (int)min((int64_t)nk, ks0 + (u_end - u));
+            for (; ok && seg < segs.n; ++seg) {
+                int64_t tile;
+                int ks0, ks1, orig;
+                segs.get(seg, tile, ks0, ks1, orig);
                 const int b = seg & 1;
                 if (seg >= 2 && !mbar_wait(&acc_empty[b], ((seg >> 1) - 1) & 1, err_flag)) {
                     abort_sh = 1;
@@ -350,7 +408,6 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                 }
                 if (!ok) break;
                 mma_commit(&acc_full[b]);
-                u += ks1 - ks0;
             }
             // Every MMA issued so far has completed before TMEM is freed.
             mma_commit(&drain_bar);
@@ -359,11 +416,12 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
     } else {
         // Epilogue warps 0-3: warp w owns TMEM lanes (tile rows) 32w .. 32w+31.
         int seg = 0;
-        for (int64_t u = u_begin; u < u_end; ++seg) {
-            const int64_t tile = u / nk;
-            const int ks0 = (int)(u % nk);
-            const int ks1 = (int)min((int64_t)nk, ks0 + (u_end - u));
-            u += ks1 - ks0;
+        for (; seg < segs.n; ++seg) {
+            int64_t tile;
+            int ks0, ks1, orig;
+            segs.get(seg, tile, ks0, ks1, orig);
+            (void)ks0;
+            (void)ks1;
             const int b = seg & 1;
             // The waiting thread sits in warp 2, a scheduler that neither the
             // producer (warp 4) nor the MMA issuer (warp 5) uses.
@@ -394,36 +452,53 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
             const int64_t first = sk.cta_of(tile * nk), last = sk.cta_of((tile + 1) * nk - 1);
             if (first == last) {
                 // The whole K range of the tile: write it.
-                if (row < M) {
-#pragma unroll
-                    for (int col = 0; col < N; ++col) {
-                        if (col < nvalid) {
-                            if (TRANS_OUT) out[(int64_t)col * out_ld + row] = v[col];
-                            else out[row * out_ld + col] = v[col];
-                        }
-                    }
-                }
+                store_row<N, TRANS_OUT>(v, 0, N, out, out_ld, row, M, nvalid, vec_out);
                 continue;
             }
-            // Partial of a shared tile: slot (CTA, its segment index).
-            const int64_t slot = (int64_t)blockIdx.x * seg_max + seg;
-            float *dst = part + (slot * kBM + warp * 32 + lane) * N;
-#pragma unroll
-            for (int i = 0; i < N; i += 4)
-                *reinterpret_cast<float4 *>(dst + i) =
-                    make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-            __threadfence();
-            epilogue_sync();
+            // Shared tile.  The arrival ticket comes first: the last CTA to
+            // arrive keeps its rows in registers and never writes them out
+            // as a partial; every other CTA writes its partial (slot: CTA,
+            // its segment index) and then counts it as written.
+            unsigned int *arrived = tickets + 2 * tile, *written = arrived + 1;
             if (threadIdx.x == 0) {
-                const unsigned int t = atomicAdd(tickets + tile, 1u);
+                const unsigned int t = atomicAdd(arrived, 1u);
                 am_last_sh = (t == (unsigned)(last - first));
             }
             epilogue_sync();
-            if (!am_last_sh) continue;
-            // Last CTA of the tile: add the other contributors' partials to
-            // the own rows still in registers, in CTA order (each thread its
-            // row, every load in flight at once), and write the tile.
-            __threadfence();
+            if (!am_last_sh) {
+                // Layout [N/4][128 rows] of float4: lanes write consecutive
+                // 16-byte words.
+                const int64_t slot = (int64_t)blockIdx.x * seg_max + orig;
+                float4 *dst = reinterpret_cast<float4 *>(part + slot * (kBM * N)) + warp * 32 + lane;
+#pragma unroll
+                for (int i = 0; i < N; i += 4)
+                    __stcg(dst + (i / 4) * kBM, make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
+                __threadfence();
+                epilogue_sync();
+                if (threadIdx.x == 0) atomicAdd(written, 1u);
+                continue;
+            }
+            // Last CTA: the others have arrived, so they are running and
+            // their partials land shortly (bounded wait on the count).
+            if (threadIdx.x == 0) {
+                const unsigned int want = (unsigned)(last - first);
+                int ok = 0;
+                for (int i = 0; i < (1 << 20); ++i) {          // ~1 s at most
+                    if (atomicAdd(written, 0u) >= want) {
+                        ok = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                if (!ok) atomicExch(err_flag, 1);
+                __threadfence();            // acquire: the partials counted above
+                seg_ok_sh = ok;
+            }
+            epilogue_sync();
+            if (!seg_ok_sh) {
+                abort_sh = 1;
+                break;
+            }
             const int nc = (int)(last - first + 1);
             if (threadIdx.x < nc && threadIdx.x < kMaxContrib) {
                 const int64_t c = first + threadIdx.x;
@@ -433,26 +508,29 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
             if (nc > kMaxContrib) {
                 if (threadIdx.x == 0) atomicExch(err_flag, 2);
             } else {
-                // Column blocks of 16 keep the register footprint small; the
-                // sum runs in CTA order whichever CTA is last (deterministic).
-                const float *myrow = part + (int64_t)(warp * 32 + lane) * N;
+                // The sum runs in CTA order whichever CTA is last
+                // (deterministic).  Up to 64 columns a thread loads a whole
+                // partial row at once (one L2 round trip per contributor);
+                // wider tiles go in column blocks of 16 to bound registers.
+                constexpr int CB = N <= 64 ? N : 16;
 #pragma unroll
-                for (int cb = 0; cb < N; cb += 16) {
-                    float sum[16];
+                for (int cb = 0; cb < N; cb += CB) {
+                    float sum[CB];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) sum[i] = 0.0f;
+                    for (int i = 0; i < CB; ++i) sum[i] = 0.0f;
                     for (int j = 0; j < nc; ++j) {
                         if (first + j == (int64_t)blockIdx.x) {
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) sum[i] += v[cb + i];
+                            for (int i = 0; i < CB; ++i) sum[i] += v[cb + i];
                         } else {
-                            const float4 *src =
-                                reinterpret_cast<const float4 *>(myrow + contrib_sh[j] + cb);
-                            float4 w[4];
+                            const float4 *src = reinterpret_cast<const float4 *>(
+                                                    part + contrib_sh[j]) +
+                                                (cb / 4) * kBM + warp * 32 + lane;
+                            float4 w[CB / 4];
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) w[i] = __ldcg(src + i);
+                            for (int i = 0; i < CB / 4; ++i) w[i] = __ldcg(src + i * kBM);
 #pragma unroll
-                            for (int i = 0; i < 4; ++i) {
+                            for (int i = 0; i < CB / 4; ++i) {
                                 sum[4 * i] += w[i].x;
                                 sum[4 * i + 1] += w[i].y;
                                 sum[4 * i + 2] += w[i].z;
@@ -460,19 +538,13 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                             }
                         }
                     }
-                    if (row < M) {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int col = cb + i;
-                            if (col < nvalid) {
-                                if (TRANS_OUT) out[(int64_t)col * out_ld + row] = sum[i];
-                                else out[row * out_ld + col] = sum[i];
-                            }
-                        }
-                    }
+                    store_row<CB, TRANS_OUT>(sum, cb, N, out, out_ld, row, M, nvalid, vec_out);
                 }
             }
-            if (threadIdx.x == 0) tickets[tile] = 0u;
+            if (threadIdx.x == 0) {
+                arrived[0] = 0u;
+                written[0] = 0u;
+            }
         }
     }
 
@@ -691,7 +763,8 @@ size_t tc_ws_bytes(int64_t M, int64_t K, int N, int precision) {
     return sizeof(float) * (size_t)(p.grid > 0 ? p.grid : 1) * p.seg_max * kBM * N;
 }
 
-int64_t tc_num_tickets(int64_t M) { return (M + kBM - 1) / kBM; }
+// Two counters per row tile: CTAs arrived, partials written.
+int64_t tc_num_tickets(int64_t M) { return 2 * ((M + kBM - 1) / kBM); }
 
 // Atoms per tile of the packed P: K rounded up to whole stages.
 int64_t tc_packed_atoms(int64_t K, int precision) {
