@@ -81,26 +81,44 @@ spmm_chunks_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ 
         for (int e = 0; e < E; ++e) acc[e] = 0.0f;
     };
 
+    // The factor rows of kBatch nonzeros are gathered before any of them is
+    // used, so their L2 latencies overlap instead of adding up.
+    constexpr int kBatch = E <= 2 ? 8 : 4;
     for (int64_t base = q0; base < q1; base += 32) {
         const int64_t q = base + lane;
         const int32_t cidx = q < q1 ? idx[q] : 0;
         const float v = q < q1 ? val[q] : 0.0f;
         const int cnt = (q1 - base) < 32 ? (int)(q1 - base) : 32;
-        for (int u = 0; u < cnt; ++u) {
-            const int64_t qu = base + u;
-            while (qu >= row_end) {          // next non-empty row
-                flush(false);
-                started_before = false;
-                ++row;
-                row_end = ptr[row + 1];
-            }
-            const int32_t cu = __shfl_sync(0xffffffffu, cidx, u);
-            const float vu = __shfl_sync(0xffffffffu, v, u);
-            const float *f = F + (int64_t)cu * rs;
+        for (int u0 = 0; u0 < cnt; u0 += kBatch) {
+            float fv[kBatch][E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int k = lane + 32 * e;
-                if (k < rs) acc[e] = fmaf(vu, f[k], acc[e]);
+            for (int j = 0; j < kBatch; ++j) {
+                const int32_t cu = __shfl_sync(0xffffffffu, cidx, (u0 + j) & 31);
+                const float *f = F + (int64_t)cu * rs;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int k = lane + 32 * e;
+                    fv[j][e] = (u0 + j < cnt && k < rs) ? __ldg(f + k) : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kBatch; ++j) {
+                const int u = u0 + j;
+                const float vu = __shfl_sync(0xffffffffu, v, u & 31);
+                if (u < cnt) {
+                    const int64_t qu = base + u;
+                    while (qu >= row_end) {          // next non-empty row
+                        flush(false);
+                        started_before = false;
+                        ++row;
+                        row_end = ptr[row + 1];
+                    }
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int k = lane + 32 * e;
+                        if (k < rs) acc[e] = fmaf(vu, fv[j][e], acc[e]);
+                    }
+                }
             }
         }
     }
