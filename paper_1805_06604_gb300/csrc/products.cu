@@ -180,21 +180,38 @@ xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     __syncthreads();
     if (!am_last) return;
     __threadfence();
+    // Each thread sums its TM*TR elements over the splits in split order,
+    // all of one split's loads in flight at once.
     const float *base = part + (int64_t)blockIdx.x * nsplit * (2 * BM * R);
-    for (int e = tid; e < BM * R; e += kThreads) {
-        float hi = 0.0f, lo = 0.0f;
-        for (int q = 0; q < nsplit; ++q) {
-            const float v = __ldcg(base + (int64_t)q * 2 * BM * R + e);
-            const float s = hi + v, bb = s - hi;
-            lo += (hi - (s - bb)) + (v - bb) + __ldcg(base + (int64_t)q * 2 * BM * R + BM * R + e);
-            hi = s;
+    constexpr int J = BM * R / kThreads;
+    static_assert(J * kThreads == BM * R, "tile must divide among the threads");
+    float fh[J], fl[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) fh[j] = fl[j] = 0.0f;
+    for (int q = 0; q < nsplit; ++q) {
+        const float *ph = base + (int64_t)q * 2 * BM * R;
+        float vh[J], vl[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            vh[j] = __ldcg(ph + tid + j * kThreads);
+            vl[j] = __ldcg(ph + BM * R + tid + j * kThreads);
         }
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const float s = fh[j] + vh[j], bb = s - fh[j];
+            fl[j] += (fh[j] - (s - bb)) + (vh[j] - bb) + vl[j];
+            fh[j] = s;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int e = tid + j * kThreads;
         const int64_t row = row0 + e / R;
         const int col = e % R;
         if (row < m && col < rs) {
-            const float c = hi + lo;
+            const float c = fh[j] + fl[j];
             C[row * rs + col] = c;
-            C_lo[row * rs + col] = (hi - c) + lo;
+            C_lo[row * rs + col] = (fh[j] - c) + fl[j];
         }
     }
     if (tid == 0) tickets[blockIdx.x] = 0u;
@@ -333,45 +350,96 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     __syncthreads();
     if (!am_last) return;
     __threadfence();
+    // Each thread sums its float4 words over the splits in split order (Kahan),
+    // all of one split's loads in flight at once.
     const float *base = part + (int64_t)blockIdx.x * nsplit * (R * BN);
-    for (int e = tid * 4; e < R * BN; e += NT * 4) {
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f), c = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int q = 0; q < nsplit; ++q) {
-            const float4 v = __ldcg(reinterpret_cast<const float4 *>(base + (int64_t)q * R * BN + e));
-            kahan_add(s.x, c.x, v.x);
-            kahan_add(s.y, c.y, v.y);
-            kahan_add(s.z, c.z, v.z);
-            kahan_add(s.w, c.w, v.w);
+    constexpr int J = R * BN / (NT * 4);
+    static_assert(J * NT * 4 == R * BN, "tile must divide among the threads");
+    float4 fs[J], fc[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) fs[j] = fc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < nsplit; ++q) {
+        const float4 *pq = reinterpret_cast<const float4 *>(base + (int64_t)q * R * BN);
+        float4 v[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) v[j] = __ldcg(pq + tid + j * NT);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            kahan_add(fs[j].x, fc[j].x, v[j].x);
+            kahan_add(fs[j].y, fc[j].y, v[j].y);
+            kahan_add(fs[j].z, fc[j].z, v[j].z);
+            kahan_add(fs[j].w, fc[j].w, v[j].w);
         }
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int e = (tid + j * NT) * 4;
         const int k = e / BN;
-        const int64_t j = col0 + e % BN;
+        const int64_t col = col0 + e % BN;
         if (k < r) {
-            const float vv[4] = {s.x - c.x, s.y - c.y, s.z - c.z, s.w - c.w};
+            const float vv[4] = {fs[j].x - fc[j].x, fs[j].y - fc[j].y, fs[j].z - fc[j].z,
+                                 fs[j].w - fc[j].w};
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (j + q < lda) A[(int64_t)k * lda + j + q] = vv[q];
+                if (col + q < lda) A[(int64_t)k * lda + col + q] = vv[q];
         }
     }
     if (tid == 0) tickets[blockIdx.x] = 0u;
 }
 
+// Splits of the reduction for a grid of tiles x nsplit CTAs of which
+// `per_sm` fit on an SM at once: the count whose waves fill the GPU best
+// (one CTA's time per SM beyond an even share is a tail), preferring fewer
+// splits unless more fill the waves by over 2 points.
+int balanced_splits(int64_t tiles, int per_sm, int64_t max_split) {
+    const int64_t slots = (int64_t)kNumSMs * (per_sm > 0 ? per_sm : 1);
+    int best = 1;
+    double best_eff = 0.0;
+    for (int64_t ns = 1; ns <= max_split; ++ns) {
+        const int64_t total = tiles * ns;
+        const int64_t waves = (total + slots - 1) / slots;
+        const double eff = (double)total / (double)(waves * slots);
+        if (eff > best_eff + 0.02) {
+            best_eff = eff;
+            best = (int)ns;
+        }
+    }
+    return best;
+}
+
+template <typename K>
+int resident_ctas(K kern, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) n = 1;
+    return n > 0 ? n : 1;
+}
+
+constexpr int kMaxWtxSplits = 64;
+constexpr int kMaxXhtSplits = 16;
+
 template <int R>
 cudaError_t wtx_launch(const float *X, int64_t m, int64_t ldx, int r, const float *W, float *A,
-                       int64_t lda, int nsplit, int64_t rows_per_split, float *part,
-                       unsigned int *tickets, cudaStream_t st) {
+                       int64_t lda, float *part, unsigned int *tickets, cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)kStages * BK * (PADN + R + 4);
     auto kern = wtx_f32_kernel<R>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((lda + BN - 1) / BN), (unsigned)nsplit);
+    static const int per_sm = resident_ctas(kern, 4 * R, smem);
+    const int64_t tiles = (lda + BN - 1) / BN;
+    int64_t max_split = (m + 8 * BK - 1) / (8 * BK);              // >= 256 rows per split
+    if (max_split > kMaxWtxSplits) max_split = kMaxWtxSplits;
+    const int want = balanced_splits(tiles, per_sm, max_split);
+    const int64_t rows_per_split = ((m + want - 1) / want + BK - 1) / BK * BK;
+    const int nsplit = (int)((m + rows_per_split - 1) / rows_per_split);
+    dim3 grid((unsigned)tiles, (unsigned)nsplit);
     kern<<<grid, 4 * R, smem, st>>>(X, m, ldx, r, W, A, lda, rows_per_split, part, tickets);
     return cudaGetLastError();
 }
 
 template <int TM, int TR>
 cudaError_t xht_launch(const float *X, int64_t m, int64_t ldx, int r, const float *H,
-                       int64_t ldh, float *C, float *C_lo, int rs, int nsplit, float *part,
+                       int64_t ldh, float *C, float *C_lo, int rs, float *part,
                        unsigned int *tickets, cudaStream_t st) {
     constexpr int BM = 16 * TM;
     constexpr int R = 8 * TR;
@@ -380,62 +448,29 @@ cudaError_t xht_launch(const float *X, int64_t m, int64_t ldx, int r, const floa
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t cols = ((ldx + nsplit - 1) / nsplit + BK - 1) / BK * BK;
-    dim3 grid((unsigned)((m + BM - 1) / BM), (unsigned)nsplit);
+    static const int per_sm = resident_ctas(kern, kThreads, smem);
+    const int64_t tiles = (m + BM - 1) / BM;
+    int64_t max_split = (ldx + 8 * BK - 1) / (8 * BK);            // >= 256 columns per split
+    if (max_split > kMaxXhtSplits) max_split = kMaxXhtSplits;
+    const int want = balanced_splits(tiles, per_sm, max_split);
+    const int64_t cols = ((ldx + want - 1) / want + BK - 1) / BK * BK;
+    const int nsplit = (int)((ldx + cols - 1) / cols);
+    dim3 grid((unsigned)tiles, (unsigned)nsplit);
     kern<<<grid, kThreads, smem, st>>>(X, m, ldx, r, H, ldh, C, C_lo, rs, cols, part, tickets);
     return cudaGetLastError();
 }
 
-// Row-tile height and column splits of C = X H^T: 64-row tiles once they
-// cover every SM (32-row tiles for r > 72, where the 64-row tile spills), and
-// enough splits of n for about two CTAs per SM.
-struct XhtPlan {
-    bool big;
-    int nsplit;
-    int64_t tiles;
-};
-
-XhtPlan plan_xht(int64_t m, int64_t ldx, int r) {
-    XhtPlan p;
-    p.big = m >= (int64_t)kNumSMs * 64 && r <= 72;
-    const int64_t bm = p.big ? 64 : 32;
-    p.tiles = (m + bm - 1) / bm;
-    int64_t want = (2 * kNumSMs + p.tiles - 1) / p.tiles;
-    const int64_t max_split = (ldx + 8 * BK - 1) / (8 * BK);   // >= 256 columns per split
-    if (want > max_split) want = max_split;
-    if (want < 1) want = 1;
-    if (want > 16) want = 16;
-    p.nsplit = (int)want;
-    return p;
-}
-
-struct WtxPlan {
-    int nsplit;
-    int64_t rows_per_split;
-    int64_t tiles;
-};
-
-WtxPlan plan_wtx(int64_t m, int64_t lda) {
-    WtxPlan p;
-    p.tiles = (lda + BN - 1) / BN;
-    int64_t want = (2 * kNumSMs + p.tiles - 1) / p.tiles;     // ~2 CTAs per SM
-    int64_t max_split = (m + 8 * BK - 1) / (8 * BK);         // >= 256 rows per split
-    if (want > max_split) want = max_split;
-    if (want < 1) want = 1;
-    if (want > 64) want = 64;
-    p.rows_per_split = ((m + want - 1) / want + BK - 1) / BK * BK;
-    p.nsplit = (int)((m + p.rows_per_split - 1) / p.rows_per_split);
-    if (p.nsplit < 1) p.nsplit = 1;
-    return p;
-}
+// Row-tile height of C = X H^T: 64-row tiles once they cover every SM
+// (32-row tiles for r > 72, where the 64-row tile spills).  The split of n
+// is chosen at launch (balanced_splits); the workspace holds the largest.
+bool xht_big(int64_t m, int r) { return m >= (int64_t)kNumSMs * 64 && r <= 72; }
 
 }  // namespace
 
 size_t wtx_ws_bytes(int64_t m, int64_t lda, int r) {
-    const WtxPlan p = plan_wtx(m, lda);
+    (void)m;
     const int R = 8 * ((r + 7) / 8);
-    if (p.nsplit == 1) return 256;
-    return sizeof(float) * (size_t)p.tiles * p.nsplit * R * BN;
+    return sizeof(float) * (size_t)((lda + BN - 1) / BN) * kMaxWtxSplits * R * BN;
 }
 
 int64_t wtx_num_tickets(int64_t lda) { return (lda + BN - 1) / BN; }
@@ -443,13 +478,11 @@ int64_t wtx_num_tickets(int64_t lda) { return (lda + BN - 1) / BN; }
 cudaError_t launch_wtx_f32(const float *X, int64_t m, int64_t lda, int64_t ldx, int r,
                            const float *W, int rs, float *A, void *ws, unsigned int *tickets,
                            cudaStream_t st) {
-    const WtxPlan p = plan_wtx(m, lda);
     float *part = static_cast<float *>(ws);
     switch (rs) {
 #define NMF_WTX_CASE(RV)                                                                      \
     case RV:                                                                                  \
-        return wtx_launch<RV>(X, m, ldx, r, W, A, lda, p.nsplit, p.rows_per_split, part,      \
-                              tickets, st);
+        return wtx_launch<RV>(X, m, ldx, r, W, A, lda, part, tickets, st);
         NMF_WTX_CASE(8) NMF_WTX_CASE(16) NMF_WTX_CASE(24) NMF_WTX_CASE(32)
         NMF_WTX_CASE(40) NMF_WTX_CASE(48) NMF_WTX_CASE(56) NMF_WTX_CASE(64)
         NMF_WTX_CASE(72) NMF_WTX_CASE(80) NMF_WTX_CASE(88) NMF_WTX_CASE(96)
@@ -460,10 +493,10 @@ cudaError_t launch_wtx_f32(const float *X, int64_t m, int64_t lda, int64_t ldx, 
 }
 
 size_t xht_ws_bytes(int64_t m, int64_t ldx, int r) {
-    const XhtPlan p = plan_xht(m, ldx, r);
-    if (p.nsplit == 1) return 256;
-    const int64_t bm = p.big ? 64 : 32;
-    return 2 * sizeof(float) * (size_t)p.tiles * p.nsplit * bm * (8 * ((r + 7) / 8));
+    (void)ldx;
+    const int64_t bm = xht_big(m, r) ? 64 : 32;
+    return 2 * sizeof(float) * (size_t)((m + bm - 1) / bm) * kMaxXhtSplits * bm *
+           (8 * ((r + 7) / 8));
 }
 
 int64_t xht_num_tickets(int64_t m) { return (m + 31) / 32; }
@@ -471,15 +504,13 @@ int64_t xht_num_tickets(int64_t m) { return (m + 31) / 32; }
 cudaError_t launch_xht_f32(const float *X, int64_t m, int64_t ldx, int r, const float *H,
                            int64_t ldh, float *C, float *C_lo, int rs, void *ws,
                            unsigned int *tickets, cudaStream_t st) {
-    const XhtPlan p = plan_xht(m, ldx, r);
+    const bool big = xht_big(m, r);
     float *part = static_cast<float *>(ws);
     switch ((r + 7) / 8) {
 #define NMF_XHT_CASE(TRV)                                                                      \
     case TRV:                                                                                  \
-        return p.big ? xht_launch<4, TRV>(X, m, ldx, r, H, ldh, C, C_lo, rs, p.nsplit, part,     \
-                                          tickets, st)                                         \
-                     : xht_launch<2, TRV>(X, m, ldx, r, H, ldh, C, C_lo, rs, p.nsplit, part,     \
-                                          tickets, st);
+        return big ? xht_launch<4, TRV>(X, m, ldx, r, H, ldh, C, C_lo, rs, part, tickets, st)   \
+                   : xht_launch<2, TRV>(X, m, ldx, r, H, ldh, C, C_lo, rs, part, tickets, st);
         NMF_XHT_CASE(1) NMF_XHT_CASE(2) NMF_XHT_CASE(3) NMF_XHT_CASE(4)
         NMF_XHT_CASE(5) NMF_XHT_CASE(6) NMF_XHT_CASE(7) NMF_XHT_CASE(8)
         NMF_XHT_CASE(9) NMF_XHT_CASE(10) NMF_XHT_CASE(11) NMF_XHT_CASE(12)
