@@ -187,32 +187,71 @@ gram_partial_kernel(const float *__restrict__ M, int64_t N, int64_t ldm, int r,
         }
 }
 
-__global__ void gram_reduce_kernel(const float *__restrict__ part, int nparts, int rs,
-                                   float *__restrict__ G) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= rs * rs) return;
+// Sum of the per-chunk partial Grams.  A CTA owns 32 consecutive entries
+// (one per lane, so each load is one coalesced row of a partial); its eight
+// warps take the partials p = w, w + 8, ... (independent loads in flight),
+// and the eight warp sums are combined in warp order (deterministic).
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(kRedWarps * 32)
+gram_reduce_kernel(const float *__restrict__ part, int nparts, int rs, float *__restrict__ G) {
+    __shared__ float sh[kRedWarps][32], sc[kRedWarps][32];
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    const int e = blockIdx.x * 32 + lane;
+    const int ne = rs * rs;
     float s = 0.0f, c = 0.0f;
-    for (int p = 0; p < nparts; ++p) kahan_add(s, c, part[(int64_t)p * rs * rs + e]);
-    G[e] = s - c;
+    if (e < ne) {
+#pragma unroll 4
+        for (int p = w; p < nparts; p += kRedWarps) kahan_add(s, c, part[(int64_t)p * ne + e]);
+    }
+    sh[w][lane] = s;
+    sc[w][lane] = c;
+    __syncthreads();
+    if (w == 0 && e < ne) {
+        float t = 0.0f, tc = 0.0f;
+        for (int q = 0; q < kRedWarps; ++q) {
+            kahan_add(t, tc, sh[q][lane]);
+            kahan_add(t, tc, -sc[q][lane]);
+        }
+        G[e] = t - tc;
+    }
 }
 
-// Pairs (hi_p, lo_p) summed exactly into G + G_lo (hi part rounded to FP32).
-__global__ void gram_reduce_exact_kernel(const float *__restrict__ part,
-                                         const float *__restrict__ part_lo, int nparts, int rs,
-                                         float *__restrict__ G, float *__restrict__ G_lo) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= rs * rs) return;
+// Pairs (hi_p, lo_p) summed exactly into G + G_lo (hi part rounded to FP32),
+// with the same decomposition.
+__global__ void __launch_bounds__(kRedWarps * 32)
+gram_reduce_exact_kernel(const float *__restrict__ part, const float *__restrict__ part_lo,
+                         int nparts, int rs, float *__restrict__ G, float *__restrict__ G_lo) {
+    __shared__ float sh[kRedWarps][32], sl[kRedWarps][32];
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    const int e = blockIdx.x * 32 + lane;
+    const int ne = rs * rs;
     float hi = 0.0f, lo = 0.0f;
-    for (int p = 0; p < nparts; ++p) {
-        float s, se;
-        two_sum(hi, part[(int64_t)p * rs * rs + e], s, se);
-        hi = s;
-        lo += se + part_lo[(int64_t)p * rs * rs + e];
+    if (e < ne) {
+#pragma unroll 4
+        for (int p = w; p < nparts; p += kRedWarps) {
+            float s, se;
+            two_sum(hi, part[(int64_t)p * ne + e], s, se);
+            hi = s;
+            lo += se + part_lo[(int64_t)p * ne + e];
+        }
     }
-    float g, ge;
-    two_sum(hi, lo, g, ge);
-    G[e] = g;
-    G_lo[e] = ge;
+    sh[w][lane] = hi;
+    sl[w][lane] = lo;
+    __syncthreads();
+    if (w == 0 && e < ne) {
+        float th = 0.0f, tl = 0.0f;
+        for (int q = 0; q < kRedWarps; ++q) {
+            float s, se;
+            two_sum(th, sh[q][lane], s, se);
+            th = s;
+            tl += se + sl[q][lane];
+        }
+        float g, ge;
+        two_sum(th, tl, g, ge);
+        G[e] = g;
+        G_lo[e] = ge;
+    }
 }
 
 struct GramPlan {
@@ -220,12 +259,13 @@ struct GramPlan {
     int64_t chunk;
 };
 
+// Chunks of whole 32-row blocks, about two CTAs per SM at most.
 GramPlan plan_gram(int64_t N) {
     GramPlan p;
-    int64_t want = (N + 63) / 64;
+    int64_t want = (N + GBK - 1) / GBK;
     if (want > 2 * kNumSMs) want = 2 * kNumSMs;
     if (want < 1) want = 1;
-    p.chunk = (N + want - 1) / want;
+    p.chunk = ((N + want - 1) / want + GBK - 1) / GBK * GBK;
     p.nparts = (int)((N + p.chunk - 1) / p.chunk);
     if (p.nparts < 1) p.nparts = 1;
     return p;
@@ -251,11 +291,12 @@ cudaError_t gram_launch(const float *M, int64_t N, int64_t ldm, int r, int rs, f
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const unsigned rgrid = (unsigned)((rs * rs + 31) / 32);
     if constexpr (EXACT)
-        gram_reduce_exact_kernel<<<(rs * rs + 255) / 256, 256, 0, st>>>(part, part_lo, p.nparts, rs,
-                                                                        G, G_lo);
+        gram_reduce_exact_kernel<<<rgrid, kRedWarps * 32, 0, st>>>(part, part_lo, p.nparts, rs, G,
+                                                                   G_lo);
     else
-        gram_reduce_kernel<<<(rs * rs + 255) / 256, 256, 0, st>>>(part, p.nparts, rs, G);
+        gram_reduce_kernel<<<rgrid, kRedWarps * 32, 0, st>>>(part, p.nparts, rs, G);
     return cudaGetLastError();
 }
 
