@@ -110,6 +110,11 @@ struct nmf_handle {
     // graph of one iteration
     cudaGraphExec_t exec = nullptr;
     DevState *h_state = nullptr;                 // pinned mirror for readback
+    // The Grams run beside the X products in the iteration graph: their own
+    // workspace, a side stream and the fork / join events of the capture.
+    float *gws = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev[2] = {}, join_ev[2] = {};
 };
 
 namespace {
@@ -128,6 +133,12 @@ void free_handle(nmf_handle *h) {
         if (q) cudaFree(q);
     if (h->h_state) cudaFreeHost(h->h_state);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->side) cudaStreamDestroy(h->side);
+    for (int i = 0; i < 2; ++i) {
+        if (h->fork_ev[i]) cudaEventDestroy(h->fork_ev[i]);
+        if (h->join_ev[i]) cudaEventDestroy(h->join_ev[i]);
+    }
+    if (h->gws) cudaFree(h->gws);
     delete h;
 }
 
@@ -215,7 +226,12 @@ cudaError_t enqueue_xht(nmf_handle *h, const float *Hsrc, cudaStream_t st) {
 
 // One outer iteration of Algorithm 2, enqueued on st.  When ev != nullptr,
 // ev[i] is recorded before phase i and ev[NMF_NUM_PHASES] after the last.
-cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = nullptr) {
+// With `overlap` (the single-instance graph), each Gram runs on the side
+// stream beside the X product it is independent of (G = W_y^T W_y beside
+// A = W_y^T X, D = H_y H_y^T beside C = X H_y^T); the next sweep waits for
+// both.  Without it (per-phase profiling, batched graphs) all runs on st.
+cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = nullptr,
+                              bool overlap = false) {
     cudaError_t e;
     auto mark = [&](int i) -> cudaError_t {
         return ev ? cudaEventRecord(ev[i], st) : cudaSuccess;
@@ -225,10 +241,17 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
         e = (expr);                   \
         if (e != cudaSuccess) return e; \
     } while (0)
+    cudaStream_t gs = overlap ? h->side : st;
+    if (overlap) {
+        NMF_STEP(cudaEventRecord(h->fork_ev[0], st));
+        NMF_STEP(cudaStreamWaitEvent(gs, h->fork_ev[0], 0));
+    }
     NMF_STEP(mark(NMF_PHASE_GRAM_W));
-    NMF_STEP(launch_gram_rows(h->Wy, h->m, h->rs, h->r, h->rs, h->G, h->ws, st));
+    NMF_STEP(launch_gram_rows(h->Wy, h->m, h->rs, h->r, h->rs, h->G, h->gws, gs));
+    if (overlap) NMF_STEP(cudaEventRecord(h->join_ev[0], gs));
     NMF_STEP(mark(NMF_PHASE_WTX));
     NMF_STEP(enqueue_wtx(h, h->Wy, st));
+    if (overlap) NMF_STEP(cudaStreamWaitEvent(st, h->join_ev[0], 0));
     NMF_STEP(mark(NMF_PHASE_HALS_H));
     HEpilogue hep{};
     hep.H_acc = h->H;
@@ -237,10 +260,16 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
     hep.hp = h->p.hp;
     NMF_STEP(launch_hals_h(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hy, h->Hn, h->lh, hep, st));
     const float *Hused = h->p.hp >= 2 ? h->Hw : h->Hn;
+    if (overlap) {
+        NMF_STEP(cudaEventRecord(h->fork_ev[1], st));
+        NMF_STEP(cudaStreamWaitEvent(gs, h->fork_ev[1], 0));
+    }
     NMF_STEP(mark(NMF_PHASE_GRAM_H));
-    NMF_STEP(launch_gram_cols(Hused, h->n, h->ld, h->r, h->rs, h->D, h->D_lo, h->ws, st));
+    NMF_STEP(launch_gram_cols(Hused, h->n, h->ld, h->r, h->rs, h->D, h->D_lo, h->gws, gs));
+    if (overlap) NMF_STEP(cudaEventRecord(h->join_ev[1], gs));
     NMF_STEP(mark(NMF_PHASE_XHT));
     NMF_STEP(enqueue_xht(h, Hused, st));
+    if (overlap) NMF_STEP(cudaStreamWaitEvent(st, h->join_ev[1], 0));
     NMF_STEP(mark(NMF_PHASE_HALS_W));
     WEpilogue wep{};
     wep.C_lo = h->C_lo;
@@ -269,7 +298,7 @@ nmf_status build_graph(nmf_handle *h) {
     }
     cudaGraph_t g = nullptr;
     NMF_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_iteration(h, h->cap);
+    cudaError_t e = enqueue_iteration(h, h->cap, nullptr, true);
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -483,6 +512,12 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
 
     const int64_t m = h->m, n = h->n, ld = h->ld, rs = h->rs;
     NMF_TRYC(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    NMF_TRYC(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+        NMF_TRYC(cudaEventCreateWithFlags(&h->fork_ev[i], cudaEventDisableTiming));
+        NMF_TRYC(cudaEventCreateWithFlags(&h->join_ev[i], cudaEventDisableTiming));
+    }
+    NMF_TRYC(cudaMalloc(&h->gws, std::max(gram_ws_bytes(m, (int)rs), gram_ws_bytes(n, (int)rs))));
     NMF_TRYC(dalloc(&h->W, m * rs));
     NMF_TRYC(dalloc(&h->Wy, m * rs));
     NMF_TRYC(dalloc(&h->Wn, m * rs));
