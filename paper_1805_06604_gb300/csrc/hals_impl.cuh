@@ -180,6 +180,9 @@ hals_kernel(int64_t items, int r, int64_t ld,
     __shared__ double red_cross[kThreads / 32], red_quad[kThreads / 32];
     __shared__ bool am_last;
     const bool err_terms = LAYOUT == kRow && wep.partials != nullptr;
+    // A programmatically dependent successor (the tensor-core X product)
+    // may start streaming X now; it waits for this grid before reading H_y.
+    asm volatile("griddepcontrol.launch_dependents;");
 
     for (int idx = threadIdx.x; idx < RP * ROW; idx += blockDim.x) {
         const int k = idx / ROW, rem = idx % ROW;

@@ -322,15 +322,36 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
 
     if (warp == 4) {
         if (lane == 0) {
-            // TMA producer: every K stage of every segment, in order.
+            // TMA producer: every K stage of every segment, in order.  X is
+            // constant, so the first ring fill of P goes out before
+            // griddepcontrol.wait (the kernel may start while its
+            // predecessor, which writes Q, still runs); the Q boxes of those
+            // stages follow the wait.
             int it = 0;
-            bool ok = true;
+            bool ok = true, waited = false;
+            int k0_def[kStages];
+            auto issue_q = [&](int s, int k0) {
+                unsigned char *qs = smem + s * Cfg::kStageBytes + Cfg::kBoxes * Cfg::kPBytes;
+#pragma unroll
+                for (int b = 0; b < Cfg::kBoxes; ++b) {
+                    // TF32: box b is K atom b.  BF16X3: box b is part b (hi, lo).
+                    const int kb = KIND == 0 ? k0 + b * Cfg::kAtomK : k0;
+                    const CUtensorMap *mq = (KIND == 1 && b == 1) ? &map_q_lo : &map_q;
+                    tma_load_2d(qs + b * Cfg::kQBytes, mq, kb, 0, &full_bar[s]);
+                }
+            };
+            auto release_q = [&]() {
+                asm volatile("griddepcontrol.wait;" ::: "memory");
+                for (int j = 0; j < it && j < kStages; ++j) issue_q(j, k0_def[j]);
+                waited = true;
+            };
             for (int sp = 0; ok && sp < segs.n; ++sp) {
                 int64_t tile;
                 int ks0, ks1, orig;
                 segs.get(sp, tile, ks0, ks1, orig);
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
                     const int s = it % kStages;
+                    if (it == kStages && !waited) release_q();
                     if (it >= kStages &&
                         !mbar_wait(&empty_bar[s], ((it / kStages) - 1) & 1, err_flag)) {
                         abort_sh = 1;
@@ -338,25 +359,23 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                         break;
                     }
                     unsigned char *st = smem + s * Cfg::kStageBytes;
-                    unsigned char *qs = st + Cfg::kBoxes * Cfg::kPBytes;
                     const int k0 = ks * Cfg::kBK;
                     mbar_expect_tx(&full_bar[s], Cfg::kStageBytes);
 #pragma unroll
                     for (int b = 0; b < Cfg::kBoxes; ++b) {
-                        // TF32: box b is K atom b.  BF16X3: box b is part b (hi, lo).
                         // P comes from its packed copy: block (tile, atom) is one
                         // contiguous, already swizzled 16 KiB image.
-                        const int kb = KIND == 0 ? k0 + b * Cfg::kAtomK : k0;
                         const int64_t atom = (int64_t)ks * Cfg::kAtoms + (KIND == 0 ? b : 0);
                         const unsigned char *src = ((KIND == 1 && b == 1) ? pk_lo : pk) +
                                                    (tile * ((int64_t)nk * Cfg::kAtoms) + atom) *
                                                        Cfg::kPBytes;
-                        const CUtensorMap *mq = (KIND == 1 && b == 1) ? &map_q_lo : &map_q;
                         bulk_load(st + b * Cfg::kPBytes, src, Cfg::kPBytes, &full_bar[s]);
-                        tma_load_2d(qs + b * Cfg::kQBytes, mq, kb, 0, &full_bar[s]);
                     }
+                    if (waited) issue_q(s, k0);
+                    else k0_def[s] = k0;
                 }
             }
+            if (!waited) release_q();
             // Copies still in flight (after an abort) land before the CTA exits.
             for (int j = it - kStages < 0 ? 0 : it - kStages; j < it; ++j)
                 mbar_wait(&full_bar[j % kStages], (j / kStages) & 1, err_flag);
@@ -632,12 +651,23 @@ cudaError_t tc_launch(const TcOperands &o, float *out, int64_t out_ld, void *ws,
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<p.grid, kTcThreads, smem, st>>>(static_cast<const unsigned char *>(o.P),
-                                           static_cast<const unsigned char *>(o.P_lo), mq, mql,
-                                           o.M, p.tiles, p.nk, o.nvalid, out,
-                                           out_ld, static_cast<float *>(ws), p.seg_max, tickets,
-                                           err_flag);
-    return cudaGetLastError();
+    // Programmatic dependent launch: the kernel may begin while the
+    // preceding kernel in the stream still runs (it waits for it before the
+    // first read of Q, see the producer).
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)p.grid);
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const unsigned char *>(o.P),
+                              static_cast<const unsigned char *>(o.P_lo), mq, mql, o.M, p.tiles,
+                              p.nk, o.nvalid, out, out_ld, static_cast<float *>(ws), p.seg_max,
+                              tickets, err_flag);
 }
 
 template <int KIND, bool TRANS>
@@ -714,6 +744,8 @@ pack_kernel(const float *__restrict__ x, int64_t rows, int64_t cols, int64_t ld,
 __global__ void split_bf16_kernel(const float *__restrict__ x, int64_t rows, int64_t cols,
                                   int64_t ld, __nv_bfloat16 *__restrict__ hi,
                                   __nv_bfloat16 *__restrict__ lo, int64_t ld_out) {
+    // Lets a programmatically dependent product kernel start its X stream.
+    asm volatile("griddepcontrol.launch_dependents;");
     const int64_t total = rows * cols;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -728,6 +760,8 @@ __global__ void split_bf16_kernel(const float *__restrict__ x, int64_t rows, int
 // out (cols x rows, row stride ld_out) = in^T (in: rows x cols, row stride ld_in).
 __global__ void transpose_kernel(const float *__restrict__ in, int64_t rows, int64_t cols,
                                  int64_t ld_in, float *__restrict__ out, int64_t ld_out) {
+    // Lets a programmatically dependent product kernel start its X stream.
+    asm volatile("griddepcontrol.launch_dependents;");
     __shared__ float tile[32][33];
     const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
