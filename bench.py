@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the image-like, batched and document-like workload lines")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip e2e / time-to-target / phase profile (quick runs)")
     return ap.parse_args()
@@ -159,6 +161,76 @@ def load_traffic(kernel: str):
     if h.hexdigest() != ent.get("digest"):
         return None
     return ent.get("bytes_per_launch")
+
+
+def timed_steps(solver, steps, stream):
+    """Seconds for `steps` graph replays of `solver`, on the device clock."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    solver.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0
+
+
+def other_workloads(nmf, torch, stream):
+    """The benchmark description's other single-GPU workloads, each measured
+    briefly: the image-like precision study, the batched instances and the
+    sparse document-like matrix."""
+    import numpy as np
+    from paper_1805_06604_gb300 import workloads as wl
+    out = {}
+    # Image-like 10304 x 4000, r = 64: FP32 / TF32 / BF16X3 products.
+    P = wl.image_like(0)
+    Xd = torch.from_numpy(P.X).cuda()
+    W0d, H0d = torch.from_numpy(P.W0).cuda(), torch.from_numpy(P.H0).cuda()
+    steps = 200
+    img = {"workload": P.name, "steps": steps}
+    for name, prec in (("fp32", nmf.NMF_PREC_FP32), ("tf32", nmf.NMF_PREC_TF32),
+                       ("bf16x3", nmf.NMF_PREC_BF16X3)):
+        sv = nmf.Solver(Xd, P.r, W0d, H0d, stream=stream, precision=prec)
+        sv.step(3)
+        t = timed_steps(sv, steps, stream)
+        W, H = sv.factors()
+        img[name] = {"iters_per_s": steps / t, "relerr_direct": direct_relerr(Xd, W, H)}
+        sv.close()
+    out["image_like_precision_study"] = img
+    del Xd, W0d, H0d
+    # Batched: 512 uneven instances, one graph per iteration vs a launch loop.
+    probs = wl.batch(count=512, seed=0)
+    b = nmf.Batch([(Q.X, Q.r, Q.W0, Q.H0) for Q in probs])
+    branches, tuned = b.schedule()
+    res = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, fn in (("graph", b.step), ("loop", b.step_loop)):
+        fn(1)
+        torch.cuda.synchronize()
+        e0.record()
+        fn(20)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / 20.0
+    b.close()
+    out["batched_512"] = {"instances": 512, "branches": branches,
+                          "graph_ms_per_iter": res["graph"], "loop_ms_per_iter": res["loop"],
+                          "speedup": res["loop"] / res["graph"],
+                          "instance_iters_per_s": 512 * 1000.0 / res["graph"]}
+    # Document-like CSR 50000 x 20000, r = 30: E-A-HALS and A-HALS.
+    P = wl.document_like(0)
+    csr = (P.rowptr, P.colidx, P.val.astype(np.float32))
+    doc = {"workload": P.name, "nnz": int(P.nnz), "steps": 300}
+    for name, kw in (("eahals", {}), ("ahals", {"beta0": 0.0})):
+        sv = nmf.Solver(None, P.r, P.W0.astype(np.float32), P.H0.astype(np.float32), csr=csr,
+                        m=P.m, n=P.n, stream=stream, **kw)
+        sv.step(3)
+        t = timed_steps(sv, 300, stream)
+        doc[name] = {"iters_per_s": 300 / t, "relerr": sv.info().relerr}
+        sv.close()
+    out["document_like_csr"] = doc
+    return out
 
 
 def direct_relerr(Xd, W, H):
@@ -407,6 +479,9 @@ def run_ours(args, world, rank, local):
         sv.close()
     line["time_to_relerr"] = ttt
     solver.close()
+
+    if not args.no_workloads:
+        line["workloads"] = other_workloads(nmf, torch, stream)
 
     if world == 1 and not args.no_cpu_baseline:
         cpu_iters = 2
