@@ -69,21 +69,32 @@ xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     const int64_t kend = min(ldx, kbeg + cols_per_split);
     const int64_t nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
 
+    // Each thread always copies the same 16-byte column c4 of rows
+    // lr, lr + 16, ... of both tiles (kThreads is a multiple of BK/4), so the
+    // addresses are formed once and advance by BK per stage.
+    constexpr int kRowsPerPass = kThreads / (BK / 4);
+    const int lr = tid / (BK / 4), c4 = tid % (BK / 4);
+    const float *xg = X + (row0 + lr) * ldx + kbeg + c4 * 4;
+    const float *hg = H + (int64_t)lr * ldh + kbeg + c4 * 4;
     auto load_stage = [&](int stage, int64_t kt) {
-        const int64_t k0 = kbeg + kt * BK;
-        float *xs = Xs + stage * BM * PADK;
-        for (int idx = tid; idx < BM * (BK / 4); idx += kThreads) {
-            const int rr = idx / (BK / 4), c4 = idx % (BK / 4);
-            const int64_t grow = row0 + rr, gcol = k0 + c4 * 4;
-            const bool ok = grow < m && gcol < kend;
-            cp_async16(xs + rr * PADK + c4 * 4, ok ? X + grow * ldx + gcol : X, ok);
+        const int64_t koff = kt * BK;
+        const bool colok = kbeg + koff + c4 * 4 < kend;
+        float *xs = Xs + stage * BM * PADK + lr * PADK + c4 * 4;
+#pragma unroll
+        for (int j = 0; j < BM / kRowsPerPass; ++j) {
+            const bool ok = colok && row0 + lr + j * kRowsPerPass < m;
+            cp_async16(xs + j * kRowsPerPass * PADK,
+                       ok ? xg + (int64_t)j * kRowsPerPass * ldx + koff : X, ok);
         }
-        float *hs = Hs + stage * R * PADK;
-        for (int idx = tid; idx < R * (BK / 4); idx += kThreads) {
-            const int kk = idx / (BK / 4), c4 = idx % (BK / 4);
-            const int64_t gcol = k0 + c4 * 4;
-            const bool ok = kk < r && gcol < kend;
-            cp_async16(hs + kk * PADK + c4 * 4, ok ? H + (int64_t)kk * ldh + gcol : H, ok);
+        float *hs = Hs + stage * R * PADK + lr * PADK + c4 * 4;
+#pragma unroll
+        for (int j = 0; j < (R + kRowsPerPass - 1) / kRowsPerPass; ++j) {
+            const int kk = lr + j * kRowsPerPass;
+            if (kk < R) {
+                const bool ok = colok && kk < r;
+                cp_async16(hs + j * kRowsPerPass * PADK,
+                           ok ? hg + (int64_t)j * kRowsPerPass * ldh + koff : H, ok);
+            }
         }
     };
 
