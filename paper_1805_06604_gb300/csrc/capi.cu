@@ -86,7 +86,10 @@ struct nmf_handle {
     float *C_lo = nullptr, *D_lo = nullptr;      // low parts for the Remark 1 terms
     // tensor-core precision modes
     int64_t ldm = 0;                             // m rounded up to 8
-    float *Wt = nullptr;                          // W_y^T (rs x ldm)
+    float *Wt = nullptr;                          // W_y'^T (rs x ldm), TF32
+    // W_y' (m x rs) and H_y' (r x ld): the factors as the tensor cores see
+    // them, from which the Grams G and D are formed in those modes.
+    float *Wq = nullptr, *Hq = nullptr;
     // Packed X for the tensor-core products: Pc for X H^T (P = X), Pa for
     // X^T W (P = X^T); the _lo arrays hold the BF16X3 low parts.
     void *Pc = nullptr, *Pc_lo = nullptr, *Pa = nullptr, *Pa_lo = nullptr;
@@ -125,7 +128,7 @@ void free_handle(nmf_handle *h) {
     void *ptrs[] = {h->X, h->rowptr, h->colidx, h->val, h->colptr, h->rowidx, h->cval, h->Ht,
                     h->carry,
                     h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn, h->Hw, h->A, h->C, h->G, h->D,
-                    h->C_lo, h->D_lo, h->Wt, h->Pc, h->Pc_lo, h->Pa, h->Pa_lo, h->Wth,
+                    h->C_lo, h->D_lo, h->Wt, h->Wq, h->Hq, h->Pc, h->Pc_lo, h->Pa, h->Pa_lo, h->Wth,
                     h->Wtl, h->Hh, h->Hl, h->tct_c, h->tct_a, h->tc_err,
                     h->fro2, h->state, h->partials, h->counter, h->tickets, h->xtickets, h->ws, h->flag,
                     h->tr_e, h->tr_beta, h->tr_acc};
@@ -171,13 +174,10 @@ cudaError_t enqueue_wtx(nmf_handle *h, const float *Wsrc, cudaStream_t st) {
     if (h->p.precision == NMF_PREC_FP32)
         return launch_wtx_f32(h->X, h->m, h->ld, h->ld, h->r, Wsrc, h->rs, h->A, h->ws,
                               h->tickets, st);
-    // A^T = X^T W_y on the tensor cores: W_y^T (rs x ldm) is rebuilt each time.
-    cudaError_t e = launch_transpose(Wsrc, h->m, h->rs, h->rs, h->Wt, h->ldm, st);
-    if (e != cudaSuccess) return e;
+    // A^T = X^T W_y' on the tensor cores; W_y'^T was made by enqueue_prep_w.
+    (void)Wsrc;
     TcOperands o{};
     if (h->p.precision == NMF_PREC_BF16X3) {
-        e = launch_split_bf16(h->Wt, h->rs, h->m, h->ldm, h->Wth, h->Wtl, h->ldm, st);
-        if (e != cudaSuccess) return e;
         o.Q = h->Wth;
         o.Q_lo = h->Wtl;
     } else {
@@ -204,14 +204,13 @@ cudaError_t enqueue_xht(nmf_handle *h, const float *Hsrc, cudaStream_t st) {
     if (h->p.precision == NMF_PREC_FP32)
         return launch_xht_f32(h->X, h->m, h->ld, h->r, Hsrc, h->ld, h->C, h->C_lo, h->rs, h->ws,
                               h->xtickets, st);
+    // C = X H_y'^T on the tensor cores; H_y' was made by enqueue_prep_h.
     TcOperands o{};
     if (h->p.precision == NMF_PREC_BF16X3) {
-        cudaError_t e = launch_split_bf16(Hsrc, h->r, h->n, h->ld, h->Hh, h->Hl, h->ld, st);
-        if (e != cudaSuccess) return e;
         o.Q = h->Hh;
         o.Q_lo = h->Hl;
     } else {
-        o.Q = Hsrc;
+        o.Q = h->Hq;
     }
     o.P = h->Pc;
     o.P_lo = h->Pc_lo;
@@ -222,6 +221,26 @@ cudaError_t enqueue_xht(nmf_handle *h, const float *Hsrc, cudaStream_t st) {
     o.N = round16(h->r);
     o.nvalid = h->rs;
     return launch_tc_product(o, h->p.precision, false, h->C, h->rs, h->ws, h->tct_c, h->tc_err, st);
+}
+
+bool tc_mode(const nmf_handle *h) { return !h->is_csr && h->p.precision != NMF_PREC_FP32; }
+
+// Tensor-core modes: the operand of the next product, made on st before the
+// Gram of the same factor is forked off (both read it).  Returns the matrix
+// the Gram is formed from: the factor itself, or its rounded copy.
+cudaError_t enqueue_prep_w(nmf_handle *h, const float *Wsrc, cudaStream_t st, const float **gram_src) {
+    *gram_src = Wsrc;
+    if (!tc_mode(h)) return cudaSuccess;
+    *gram_src = h->Wq;
+    return launch_tc_prep_w(Wsrc, h->m, h->rs, h->rs, h->p.precision, h->Wq, h->Wt, h->Wth, h->Wtl,
+                            h->ldm, st);
+}
+
+cudaError_t enqueue_prep_h(nmf_handle *h, const float *Hsrc, cudaStream_t st, const float **gram_src) {
+    *gram_src = Hsrc;
+    if (!tc_mode(h)) return cudaSuccess;
+    *gram_src = h->Hq;
+    return launch_tc_prep_h(Hsrc, h->r, h->ld, h->ld, h->p.precision, h->Hq, h->Hh, h->Hl, st);
 }
 
 // One outer iteration of Algorithm 2, enqueued on st.  When ev != nullptr,
@@ -242,12 +261,15 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
         if (e != cudaSuccess) return e; \
     } while (0)
     cudaStream_t gs = overlap ? h->side : st;
+    // (Tensor-core modes: the operand preparation counts as the Gram phase.)
+    NMF_STEP(mark(NMF_PHASE_GRAM_W));
+    const float *Wg = nullptr;
+    NMF_STEP(enqueue_prep_w(h, h->Wy, st, &Wg));
     if (overlap) {
         NMF_STEP(cudaEventRecord(h->fork_ev[0], st));
         NMF_STEP(cudaStreamWaitEvent(gs, h->fork_ev[0], 0));
     }
-    NMF_STEP(mark(NMF_PHASE_GRAM_W));
-    NMF_STEP(launch_gram_rows(h->Wy, h->m, h->rs, h->r, h->rs, h->G, h->gws, gs));
+    NMF_STEP(launch_gram_rows(Wg, h->m, h->rs, h->r, h->rs, h->G, h->gws, gs));
     if (overlap) NMF_STEP(cudaEventRecord(h->join_ev[0], gs));
     NMF_STEP(mark(NMF_PHASE_WTX));
     NMF_STEP(enqueue_wtx(h, h->Wy, st));
@@ -260,12 +282,14 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
     hep.hp = h->p.hp;
     NMF_STEP(launch_hals_h(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hy, h->Hn, h->lh, hep, st));
     const float *Hused = h->p.hp >= 2 ? h->Hw : h->Hn;
+    NMF_STEP(mark(NMF_PHASE_GRAM_H));
+    const float *Hg = nullptr;
+    NMF_STEP(enqueue_prep_h(h, Hused, st, &Hg));
     if (overlap) {
         NMF_STEP(cudaEventRecord(h->fork_ev[1], st));
         NMF_STEP(cudaStreamWaitEvent(gs, h->fork_ev[1], 0));
     }
-    NMF_STEP(mark(NMF_PHASE_GRAM_H));
-    NMF_STEP(launch_gram_cols(Hused, h->n, h->ld, h->r, h->rs, h->D, h->D_lo, h->gws, gs));
+    NMF_STEP(launch_gram_cols(Hg, h->n, h->ld, h->r, h->rs, h->D, h->D_lo, h->gws, gs));
     if (overlap) NMF_STEP(cudaEventRecord(h->join_ev[1], gs));
     NMF_STEP(mark(NMF_PHASE_XHT));
     NMF_STEP(enqueue_xht(h, Hused, st));
@@ -645,6 +669,10 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
             NMF_TRYC(launch_tc_pack(h->X, m, n, ld, true, p.precision, h->Pa, h->Pa_lo, st));
             NMF_TRYC(dalloc(&h->Wt, rs * h->ldm));
             NMF_TRYC(cudaMemsetAsync(h->Wt, 0, sizeof(float) * rs * h->ldm, st));
+            NMF_TRYC(dalloc(&h->Wq, m * rs));
+            NMF_TRYC(cudaMemsetAsync(h->Wq, 0, sizeof(float) * m * rs, st));
+            NMF_TRYC(dalloc(&h->Hq, r * ld));
+            NMF_TRYC(cudaMemsetAsync(h->Hq, 0, sizeof(float) * r * ld, st));
             NMF_TRYC(dalloc(&h->tct_c, tc_num_tickets(m)));
             NMF_TRYC(dalloc(&h->tct_a, tc_num_tickets(n)));
             NMF_TRYC(dalloc(&h->tc_err, 1));
@@ -665,7 +693,9 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     }
 
     // e(0) = ||X - W H||_F via Remark 1 (Algorithm 2 step 1).
-    NMF_TRYC(launch_gram_cols(h->H, n, ld, r, (int)rs, h->D, h->D_lo, h->ws, st));
+    const float *H0g = nullptr;
+    NMF_TRYC(enqueue_prep_h(h, h->H, st, &H0g));
+    NMF_TRYC(launch_gram_cols(H0g, n, ld, r, (int)rs, h->D, h->D_lo, h->ws, st));
     NMF_TRYC(enqueue_xht(h, h->H, st));
     NMF_TRYC(launch_init_state(m, r, (int)rs, h->W, h->C, h->C_lo, h->D, h->D_lo, h->fro2,
                                h->state, p.beta0, h->partials, st));
@@ -712,8 +742,8 @@ nmf_status nmf_get_info(nmf_handle *h, nmf_info *info) {
     // W sweeps (1) + finalize (1); CSR: each product is 2 kernels (+ a
     // memset) and X H^T adds the H transpose.
     info->launches_per_iter = h->is_csr ? 12 : 9;
-    if (h->p.precision == NMF_PREC_TF32) info->launches_per_iter = 10;     // + W_y transpose
-    if (h->p.precision == NMF_PREC_BF16X3) info->launches_per_iter = 12;   // + transpose, 2 splits
+    // Tensor-core modes: + the W_y' and H_y' operand preparations.
+    if (tc_mode(h)) info->launches_per_iter = 11;
     if (h->tc_err) {
         int e = 0;
         NMF_CUDA(cudaMemcpy(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -910,7 +940,9 @@ nmf_status nmf_matmul_nt(const float *P, int64_t M, int64_t K, int64_t ldp, cons
     int *err = nullptr;
     void *ph = nullptr, *pl = nullptr;
     __nv_bfloat16 *qh = nullptr, *ql = nullptr;
+    float *qf = nullptr;
     auto cleanup = [&]() {
+        cudaFree(qf);
         cudaFree(ws);
         cudaFree(tickets);
         cudaFree(err);
@@ -937,15 +969,15 @@ nmf_status nmf_matmul_nt(const float *P, int64_t M, int64_t K, int64_t ldp, cons
     if (e == cudaSuccess) e = cudaMalloc(&ph, pb);
     if (e == cudaSuccess && bf) e = cudaMalloc(&pl, pb);
     if (e == cudaSuccess) e = launch_tc_pack(P, M, K, ldp, false, precision, ph, pl, st);
+    // Q as the tensor cores see it (nearest TF32 values, or the hi/lo pair).
+    if (e == cudaSuccess) e = cudaMalloc(&qf, sizeof(float) * q_rows * ldq);
     if (e == cudaSuccess && bf) {
         e = cudaMalloc(&qh, sizeof(__nv_bfloat16) * q_rows * ldq);
         if (e == cudaSuccess) e = cudaMalloc(&ql, sizeof(__nv_bfloat16) * q_rows * ldq);
-        if (e == cudaSuccess) e = launch_split_bf16(Q, q_rows, K, ldq, qh, ql, ldq, st);
-        o.Q = qh;
-        o.Q_lo = ql;
-    } else {
-        o.Q = Q;
     }
+    if (e == cudaSuccess) e = launch_tc_prep_h(Q, q_rows, K, ldq, precision, qf, qh, ql, st);
+    o.Q = bf ? static_cast<const void *>(qh) : static_cast<const void *>(qf);
+    o.Q_lo = ql;
     o.P = ph;
     o.P_lo = pl;
     if (e == cudaSuccess) e = launch_tc_product(o, precision, false, out, ldo, ws, tickets, err, st);

@@ -175,11 +175,18 @@ bool tc_available();
 cudaError_t launch_tc_product(const TcOperands &o, int precision, bool transposed_out, float *out,
                               int64_t out_ld, void *ws, unsigned int *tickets, int *err_flag,
                               cudaStream_t st);
-cudaError_t launch_split_bf16(const float *x, int64_t rows, int64_t cols, int64_t ld,
-                              __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ld_out,
-                              cudaStream_t st);
-cudaError_t launch_transpose(const float *in, int64_t rows, int64_t cols, int64_t ld_in,
-                             float *out, int64_t ld_out, cudaStream_t st);
+// The factor operands as the tensor cores see them (TF32: nearest TF32
+// value; BF16X3: hi + lo), so that products and Grams use one matrix.
+// H_y (rows x cols, row stride ld): q (and hi / lo) in the same layout.
+// W_y (rows x cols, row stride ld_in): q in the same layout, plus the
+// transposed operand (cols x rows, stride ld_t): qt for TF32, ht / lt for
+// BF16X3.
+cudaError_t launch_tc_prep_h(const float *H, int64_t rows, int64_t cols, int64_t ld,
+                             int precision, float *q, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                             cudaStream_t st);
+cudaError_t launch_tc_prep_w(const float *W, int64_t rows, int64_t cols, int64_t ld_in,
+                             int precision, float *q, float *qt, __nv_bfloat16 *ht,
+                             __nv_bfloat16 *lt, int64_t ld_t, cudaStream_t st);
 
 // Records `msg` as the calling thread's nmf_last_error() and returns s.
 nmf_status set_error(nmf_status s, const char *msg);

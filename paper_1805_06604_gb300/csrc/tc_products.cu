@@ -9,13 +9,16 @@
 // the (128-row tile of P, 64-element K stage) units, so every SM streams the
 // same number of bytes of X.  A stage (two 128-byte-wide boxes of P and Q)
 // arrives by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a shared-
-// memory ring; one thread issues tcgen05.mma into an FP32 accumulator in
-// tensor memory, two of which alternate between the tiles a CTA touches;
-// four warps read a finished accumulator (tcgen05.ld) and write the tile, or
-// a partial of it that the tile's last CTA (atomic ticket) adds to the other
-// partials in CTA order -- deterministic.
+// memory ring; one thread issues tcgen05.mma into FP32 accumulators in
+// tensor memory.  Up to N = 64 each K stage has its own accumulator (four in
+// flight), which four epilogue warps read (tcgen05.ld) and add into a
+// compensated register sum; wider tiles accumulate a whole segment in one of
+// two accumulators.  The epilogue writes the tile, or a partial of it that
+// the tile's last CTA (atomic ticket) adds to the other partials in CTA
+// order -- deterministic.
 //
-//  TF32:     D += P Q^T with the operands read as TF32 (one product).
+//  TF32:     D += P Q^T with the operands rounded to the nearest TF32 value
+//            (X when it is packed, the factor by prep_*_kernel).
 //  BF16X3:   P and Q are held as hi/lo BF16 pairs (x ~ hi + lo); three
 //            products hi.hi + hi.lo + lo.hi accumulate in FP32.
 //
@@ -109,6 +112,17 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+// Nearest TF32 value of x (ties away from zero).  The MMA reads an FP32
+// operand's top 19 bits, i.e. it truncates: on nonnegative data that is a
+// bias of about -2^-11 relative in every product, which the Remark 1 error
+// (a difference of nearly equal terms) turns into an offset of order
+// 1e-3 ||X||^2.  Operands are rounded to nearest before they reach it.
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return __uint_as_float(u);
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
 // bytes, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -181,7 +195,15 @@ struct TcCfg {
     static constexpr int kKSteps = kAtom / 32;                 // MMAs per atom (32 bytes of K)
     static constexpr uint32_t kIdesc = instr_desc(KIND == 0 ? 2 : 1, kBM, N);
     static constexpr int kAccCols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);   // one accumulator
-    static constexpr int kTmemCols = 2 * kAccCols;             // double-buffered
+    // Up to N = 64 every K stage gets a fresh accumulator, which the
+    // epilogue adds into a compensated (Kahan) register sum: the tensor
+    // core's FP32 accumulation then spans only the 64 K of one stage, and
+    // the result is accurate to a few units of FP32 rounding whatever K.
+    // Wider tiles (2N sum registers would not fit) accumulate a whole
+    // segment in tensor memory.
+    static constexpr bool kComp = N <= 64;
+    static constexpr int kNumAcc = kComp ? 4 : 2;              // accumulators in flight
+    static constexpr int kTmemCols = kNumAcc * kAccCols;
     static constexpr int kFit = (200 * 1024) / kStageBytes;
     static constexpr int kStages = kFit < 2 ? 2 : (kFit > 6 ? 6 : kFit);
     static_assert(kStages * kStageBytes + 2048 <= 227 * 1024, "stage ring exceeds shared memory");
@@ -282,7 +304,8 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
-    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain_bar;
+    constexpr int kNumAcc = Cfg::kNumAcc;
+    __shared__ __align__(8) uint64_t acc_full[kNumAcc], acc_empty[kNumAcc], drain_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh, seg_ok_sh;
     __shared__ bool am_last_sh;
@@ -300,7 +323,7 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kNumAcc; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 4);
         }
@@ -389,15 +412,27 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                 int64_t tile;
                 int ks0, ks1, orig;
                 segs.get(seg, tile, ks0, ks1, orig);
-                const int b = seg & 1;
-                if (seg >= 2 && !mbar_wait(&acc_empty[b], ((seg >> 1) - 1) & 1, err_flag)) {
+                // Accumulator of the segment (kComp: of each stage, below).
+                int b = seg % kNumAcc;
+                if (!Cfg::kComp && seg >= kNumAcc &&
+                    !mbar_wait(&acc_empty[b], ((seg / kNumAcc) - 1) & 1, err_flag)) {
                     abort_sh = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t d = tmem + (uint32_t)(b * Cfg::kAccCols);
+                uint32_t d = tmem + (uint32_t)(b * Cfg::kAccCols);
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
                     const int s = it % kStages;
+                    if constexpr (Cfg::kComp) {
+                        b = it % kNumAcc;
+                        d = tmem + (uint32_t)(b * Cfg::kAccCols);
+                        if (it >= kNumAcc &&
+                            !mbar_wait(&acc_empty[b], ((it / kNumAcc) - 1) & 1, err_flag)) {
+                            abort_sh = 1;
+                            ok = false;
+                            break;
+                        }
+                    }
                     if (!mbar_wait(&full_bar[s], (it / kStages) & 1, err_flag)) {
                         abort_sh = 1;
                         ok = false;
@@ -411,7 +446,8 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
 #pragma unroll
                         for (int kk = 0; kk < Cfg::kKSteps; ++kk) {
                             const uint32_t off = kk * 32;
-                            const uint32_t acc = (ks > ks0 || a > 0 || kk > 0) ? 1u : 0u;
+                            const uint32_t acc =
+                                ((!Cfg::kComp && ks > ks0) || a > 0 || kk > 0) ? 1u : 0u;
                             const uint32_t ph = base + a * Cfg::kPBytes + off;
                             const uint32_t qh = qbase + a * Cfg::kQBytes + off;
                             mma<KIND>(d, smem_desc(ph), smem_desc(qh), Cfg::kIdesc, acc);
@@ -424,9 +460,10 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                         }
                     }
                     mma_commit(&empty_bar[s]);
+                    if constexpr (Cfg::kComp) mma_commit(&acc_full[b]);
                 }
                 if (!ok) break;
-                mma_commit(&acc_full[b]);
+                if constexpr (!Cfg::kComp) mma_commit(&acc_full[b]);
             }
             // Every MMA issued so far has completed before TMEM is freed.
             mma_commit(&drain_bar);
@@ -434,37 +471,80 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
         }
     } else {
         // Epilogue warps 0-3: warp w owns TMEM lanes (tile rows) 32w .. 32w+31.
-        int seg = 0;
+        int seg = 0, it = 0;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        // One accumulator is complete (bounded wait by one thread, in warp 2:
+        // a scheduler that neither the producer, warp 4, nor the MMA issuer,
+        // warp 5, uses); the flag reaches all four warps.
+        auto acc_ready = [&](int b, uint32_t parity, bool sleep) -> bool {
+            if (threadIdx.x == 64)
+                seg_ok_sh = sleep ? mbar_wait_sleep(&acc_full[b], parity, err_flag)
+                                  : mbar_wait(&acc_full[b], parity, err_flag);
+            epilogue_sync();
+            const int ok = seg_ok_sh;
+            epilogue_sync();            // all four warps read the flag before it is rewritten
+            if (ok) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            return ok != 0;
+        };
+        auto acc_release = [&](int b) {
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        };
         for (; seg < segs.n; ++seg) {
             int64_t tile;
             int ks0, ks1, orig;
             segs.get(seg, tile, ks0, ks1, orig);
-            (void)ks0;
-            (void)ks1;
-            const int b = seg & 1;
-            // The waiting thread sits in warp 2, a scheduler that neither the
-            // producer (warp 4) nor the MMA issuer (warp 5) uses.
-            if (threadIdx.x == 64) seg_ok_sh = mbar_wait_sleep(&acc_full[b], (seg >> 1) & 1, err_flag);
-            epilogue_sync();
-            const int seg_ok = seg_ok_sh;
-            epilogue_sync();            // all four warps read the flag before it is rewritten
+            float v[N];
+            bool seg_ok = true;
+            if constexpr (Cfg::kComp) {
+                // Each stage's accumulator is added into sum - cor (Kahan).
+                float sum[N], cor[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) sum[i] = cor[i] = 0.0f;
+                for (int ks = ks0; ks < ks1; ++ks, ++it) {
+                    const int b = it % kNumAcc;
+                    if (!acc_ready(b, (it / kNumAcc) & 1, false)) {
+                        seg_ok = false;
+                        break;
+                    }
+#pragma unroll
+                    for (int c0 = 0; c0 < N; c0 += 16) {
+                        float w16[16];
+                        tmem_ld16(lane_base + (uint32_t)(b * Cfg::kAccCols + c0), w16);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float y = w16[i] - cor[c0 + i];
+                            const float t = sum[c0 + i] + y;
+                            cor[c0 + i] = (t - sum[c0 + i]) - y;
+                            sum[c0 + i] = t;
+                        }
+                    }
+                    acc_release(b);
+                }
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[i] = sum[i] - cor[i];
+            } else {
+                (void)ks0;
+                (void)ks1;
+                const int b = seg % kNumAcc;
+                if (acc_ready(b, (seg / kNumAcc) & 1, true)) {
+#pragma unroll
+                    for (int c0 = 0; c0 < N; c0 += 16) {
+                        float w16[16];
+                        tmem_ld16(lane_base + (uint32_t)(b * Cfg::kAccCols + c0), w16);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[c0 + i] = w16[i];
+                    }
+                    acc_release(b);
+                } else {
+                    seg_ok = false;
+                }
+            }
             if (!seg_ok) {
                 abort_sh = 1;
                 break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float v[N];
-#pragma unroll
-            for (int c0 = 0; c0 < N; c0 += 16) {
-                float w16[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * Cfg::kAccCols + c0),
-                          w16);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[c0 + i] = w16[i];
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[b]);
 
             const int64_t row0 = tile * kBM;
             const int64_t row = row0 + warp * 32 + lane;
@@ -735,47 +815,121 @@ pack_kernel(const float *__restrict__ x, int64_t rows, int64_t cols, int64_t ld,
             *reinterpret_cast<uint4 *>(blk_hi + pos) = *reinterpret_cast<const uint4 *>(h);
             *reinterpret_cast<uint4 *>(blk_lo + pos) = *reinterpret_cast<const uint4 *>(l);
         } else {
-            *reinterpret_cast<float4 *>(blk_hi + pos) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4 *>(blk_hi + pos) =
+                make_float4(tf32_rna(v[0]), tf32_rna(v[1]), tf32_rna(v[2]), tf32_rna(v[3]));
         }
     }
 }
 
-// hi = bf16(x), lo = bf16(x - hi), element-wise over rows x cols (row stride ld).
-__global__ void split_bf16_kernel(const float *__restrict__ x, int64_t rows, int64_t cols,
-                                  int64_t ld, __nv_bfloat16 *__restrict__ hi,
-                                  __nv_bfloat16 *__restrict__ lo, int64_t ld_out) {
-    // Lets a programmatically dependent product kernel start its X stream.
-    asm volatile("griddepcontrol.launch_dependents;");
-    const int64_t total = rows * cols;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q / cols, j = q % cols;
-        const float v = x[i * ld + j];
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        hi[i * ld_out + j] = h;
-        lo[i * ld_out + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+// The factor operand of a tensor-core product as the tensor cores see it.
+// TF32: q = tf32_rna(x).  BF16X3: hi = bf16(x), lo = bf16(x - hi) and
+// q = hi + lo.  The Gram of the same factor is then formed from q, so that
+// the product, the Gram and the Remark 1 error they feed all refer to one
+// matrix; with the product and the Gram rounded differently the error
+// carries a random term of about u ||X||^2 / sqrt(r n) per iteration (u
+// the operand rounding), far above the differences the restart test has
+// to resolve near convergence.
+template <bool BF>
+__device__ __forceinline__ float operand_value(float x, __nv_bfloat16 &h, __nv_bfloat16 &l) {
+    if constexpr (BF) {
+        h = __float2bfloat16_rn(x);
+        l = __float2bfloat16_rn(x - __bfloat162float(h));
+        return __bfloat162float(h) + __bfloat162float(l);
+    } else {
+        return tf32_rna(x);
     }
 }
 
-// out (cols x rows, row stride ld_out) = in^T (in: rows x cols, row stride ld_in).
-__global__ void transpose_kernel(const float *__restrict__ in, int64_t rows, int64_t cols,
-                                 int64_t ld_in, float *__restrict__ out, int64_t ld_out) {
+// Element-wise over rows x cols (row stride ld; H_y is r x ld): q, and for
+// BF16X3 the hi / lo arrays, in the same layout.
+template <bool BF>
+__global__ void __launch_bounds__(256)
+prep_h_kernel(const float *__restrict__ x, int64_t rows, int64_t cols, int64_t ld,
+              float *__restrict__ q, __nv_bfloat16 *__restrict__ hi,
+              __nv_bfloat16 *__restrict__ lo) {
     // Lets a programmatically dependent product kernel start its X stream.
     asm volatile("griddepcontrol.launch_dependents;");
-    __shared__ float tile[32][33];
-    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const int64_t count = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = (e / cols) * ld + e % cols;
+        __nv_bfloat16 h, l;
+        q[i] = operand_value<BF>(x[i], h, l);
+        if constexpr (BF) {
+            hi[i] = h;
+            lo[i] = l;
+        }
+    }
+}
+
+// W_y (rows x cols, row stride ld_in): q in the same layout (for the Gram),
+// and the transposed operand (cols x rows, row stride ld_t): q^T for TF32,
+// hi^T / lo^T for BF16X3.
+template <bool BF>
+__global__ void prep_w_kernel(const float *__restrict__ x, int64_t rows, int64_t cols,
+                              int64_t ld_in, float *__restrict__ q, float *__restrict__ qt,
+                              __nv_bfloat16 *__restrict__ ht, __nv_bfloat16 *__restrict__ lt,
+                              int64_t ld_t) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    __shared__ float tq[32][33];
+    __shared__ __nv_bfloat16 th[32][34], tl[32][34];
+    const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int64_t r = r0 + y, c = c0 + threadIdx.x;
-        tile[y][threadIdx.x] = (r < rows && c < cols) ? in[r * ld_in + c] : 0.0f;
+        const int64_t rr = r0 + y, cc = c0 + threadIdx.x;
+        float v = 0.0f;
+        __nv_bfloat16 h = __float2bfloat16_rn(0.0f), l = h;
+        if (rr < rows && cc < cols) {
+            v = operand_value<BF>(x[rr * ld_in + cc], h, l);
+            q[rr * ld_in + cc] = v;
+        }
+        tq[y][threadIdx.x] = v;
+        th[y][threadIdx.x] = h;
+        tl[y][threadIdx.x] = l;
     }
     __syncthreads();
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int64_t c = c0 + y, r = r0 + threadIdx.x;
-        if (c < cols && r < rows) out[c * ld_out + r] = tile[threadIdx.x][y];
+        const int64_t cc = c0 + y, rr = r0 + threadIdx.x;
+        if (cc < cols && rr < rows) {
+            if constexpr (BF) {
+                ht[cc * ld_t + rr] = th[threadIdx.x][y];
+                lt[cc * ld_t + rr] = tl[threadIdx.x][y];
+            } else {
+                qt[cc * ld_t + rr] = tq[threadIdx.x][y];
+            }
+        }
     }
 }
 
 }  // namespace
+
+cudaError_t launch_tc_prep_h(const float *H, int64_t rows, int64_t cols, int64_t ld,
+                             int precision, float *q, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                             cudaStream_t st) {
+    int64_t blocks = (rows * cols + 255) / 256;
+    if (blocks > 4 * kNumSMs) blocks = 4 * kNumSMs;
+    if (blocks < 1) blocks = 1;
+    if (precision == NMF_PREC_TF32)
+        prep_h_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(H, rows, cols, ld, q, hi, lo);
+    else if (precision == NMF_PREC_BF16X3)
+        prep_h_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(H, rows, cols, ld, q, hi, lo);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_prep_w(const float *W, int64_t rows, int64_t cols, int64_t ld_in,
+                             int precision, float *q, float *qt, __nv_bfloat16 *ht,
+                             __nv_bfloat16 *lt, int64_t ld_t, cudaStream_t st) {
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    if (precision == NMF_PREC_TF32)
+        prep_w_kernel<false><<<grid, dim3(32, 8), 0, st>>>(W, rows, cols, ld_in, q, qt, ht, lt, ld_t);
+    else if (precision == NMF_PREC_BF16X3)
+        prep_w_kernel<true><<<grid, dim3(32, 8), 0, st>>>(W, rows, cols, ld_in, q, qt, ht, lt, ld_t);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
 
 template <int KIND>
 TcPlan plan_dispatch(int64_t M, int64_t K, int N) {
@@ -844,23 +998,6 @@ cudaError_t launch_tc_product(const TcOperands &o, int precision, bool transpose
         return transposed_out ? tc_dispatch_n<1, true>(o, out, out_ld, ws, tickets, err_flag, st)
                               : tc_dispatch_n<1, false>(o, out, out_ld, ws, tickets, err_flag, st);
     return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_split_bf16(const float *x, int64_t rows, int64_t cols, int64_t ld,
-                              __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ld_out,
-                              cudaStream_t st) {
-    int64_t blocks = (rows * cols + 255) / 256;
-    if (blocks > 8 * kNumSMs) blocks = 8 * kNumSMs;
-    if (blocks < 1) blocks = 1;
-    split_bf16_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, rows, cols, ld, hi, lo, ld_out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_transpose(const float *in, int64_t rows, int64_t cols, int64_t ld_in,
-                             float *out, int64_t ld_out, cudaStream_t st) {
-    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-    transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(in, rows, cols, ld_in, out, ld_out);
-    return cudaGetLastError();
 }
 
 }  // namespace nmfg
