@@ -305,7 +305,7 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
     constexpr int kNumAcc = Cfg::kNumAcc;
-    __shared__ __align__(8) uint64_t acc_full[kNumAcc], acc_empty[kNumAcc], drain_bar;
+    __shared__ __align__(8) uint64_t acc_full[kNumAcc], acc_empty[kNumAcc], drain_bar, fix_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh, seg_ok_sh;
     __shared__ bool am_last_sh;
@@ -328,6 +328,7 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
             mbar_init(&acc_empty[b], 4);
         }
         mbar_init(&drain_bar, 1);
+        mbar_init(&fix_bar, 1);
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -472,6 +473,7 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
     } else {
         // Epilogue warps 0-3: warp w owns TMEM lanes (tile rows) 32w .. 32w+31.
         int seg = 0, it = 0;
+        bool fix_used = false;          // fix_bar serves one staged fix-up
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         // One accumulator is complete (bounded wait by one thread, in warp 2:
         // a scheduler that neither the producer, warp 4, nor the MMA issuer,
@@ -604,8 +606,59 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                 contrib_sh[threadIdx.x] = (c * seg_max + (tile - sk.begin(c) / nk)) * (kBM * N);
             }
             epilogue_sync();
+            // In the CTA's last segment the stage ring is idle (every stage
+            // was consumed by an MMA that has completed), so the other
+            // partials are fetched into it all at once (one bulk copy each,
+            // one round trip) instead of one L2 round trip per contributor.
+            constexpr int kTileBytes = kBM * N * (int)sizeof(float);
+            const bool staged = N <= 64 && seg == segs.n - 1 && !fix_used &&
+                                (int64_t)(nc - 1) * kTileBytes <= (int64_t)kStages * Cfg::kStageBytes;
+            if (staged && nc <= kMaxContrib) {
+                if (threadIdx.x == 0) {
+                    // Generic-proxy writes of the other CTAs (acquired above)
+                    // before the async-proxy reads below.
+                    asm volatile("fence.proxy.async;" ::: "memory");
+                    mbar_expect_tx(&fix_bar, (uint32_t)((nc - 1) * kTileBytes));
+                    for (int j = 0, q = 0; j < nc; ++j)
+                        if (first + j != (int64_t)blockIdx.x)
+                            bulk_load(smem + (q++) * kTileBytes, part + contrib_sh[j], kTileBytes,
+                                      &fix_bar);
+                }
+                if (threadIdx.x == 64) seg_ok_sh = mbar_wait(&fix_bar, 0, err_flag);
+                epilogue_sync();
+                const int fetched = seg_ok_sh;
+                epilogue_sync();
+                fix_used = true;
+                if (!fetched) {
+                    abort_sh = 1;
+                    break;
+                }
+            }
             if (nc > kMaxContrib) {
                 if (threadIdx.x == 0) atomicExch(err_flag, 2);
+            } else if (N <= 64 && staged) {
+                // Same order and arithmetic as below, from shared memory.
+                const float4 *stg = reinterpret_cast<const float4 *>(smem) + warp * 32 + lane;
+                float sum[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) sum[i] = 0.0f;
+                for (int j = 0, q = 0; j < nc; ++j) {
+                    if (first + j == (int64_t)blockIdx.x) {
+#pragma unroll
+                        for (int i = 0; i < N; ++i) sum[i] += v[i];
+                    } else {
+                        const float4 *src = stg + (int64_t)(q++) * (kTileBytes / 16);
+#pragma unroll
+                        for (int i = 0; i < N / 4; ++i) {
+                            const float4 w = src[i * kBM];
+                            sum[4 * i] += w.x;
+                            sum[4 * i + 1] += w.y;
+                            sum[4 * i + 2] += w.z;
+                            sum[4 * i + 3] += w.w;
+                        }
+                    }
+                }
+                store_row<N, TRANS_OUT>(sum, 0, N, out, out_ld, row, M, nvalid, vec_out);
             } else {
                 // The sum runs in CTA order whichever CTA is last
                 // (deterministic).  Up to 64 columns a thread loads a whole
