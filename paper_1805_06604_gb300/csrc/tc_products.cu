@@ -202,6 +202,7 @@ struct TcCfg {
     // Wider tiles (2N sum registers would not fit) accumulate a whole
     // segment in tensor memory.
     static constexpr bool kComp = N <= 64;
+    static constexpr int kGroup = 1;                           // K stages per drained accumulator
     static constexpr int kNumAcc = kComp ? 4 : 2;              // accumulators in flight
     static constexpr int kTmemCols = kNumAcc * kAccCols;
     static constexpr int kFit = (200 * 1024) / kStageBytes;
@@ -407,7 +408,7 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
     } else if (warp == 5) {
         if (lane == 0) {
             // MMA issuer.
-            int it = 0, seg = 0;
+            int it = 0, seg = 0, grp = 0;
             bool ok = true;
             for (; ok && seg < segs.n; ++seg) {
                 int64_t tile;
@@ -424,14 +425,20 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                 uint32_t d = tmem + (uint32_t)(b * Cfg::kAccCols);
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
                     const int s = it % kStages;
+                    // kComp: a group of kGroup stages (cut at the segment's
+                    // end) accumulates into accumulator grp % kNumAcc.
+                    const bool g_first = (ks - ks0) % Cfg::kGroup == 0;
+                    const bool g_last = (ks - ks0) % Cfg::kGroup == Cfg::kGroup - 1 || ks == ks1 - 1;
                     if constexpr (Cfg::kComp) {
-                        b = it % kNumAcc;
-                        d = tmem + (uint32_t)(b * Cfg::kAccCols);
-                        if (it >= kNumAcc &&
-                            !mbar_wait(&acc_empty[b], ((it / kNumAcc) - 1) & 1, err_flag)) {
-                            abort_sh = 1;
-                            ok = false;
-                            break;
+                        if (g_first) {
+                            b = grp % kNumAcc;
+                            d = tmem + (uint32_t)(b * Cfg::kAccCols);
+                            if (grp >= kNumAcc &&
+                                !mbar_wait(&acc_empty[b], ((grp / kNumAcc) - 1) & 1, err_flag)) {
+                                abort_sh = 1;
+                                ok = false;
+                                break;
+                            }
                         }
                     }
                     if (!mbar_wait(&full_bar[s], (it / kStages) & 1, err_flag)) {
@@ -448,7 +455,7 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                         for (int kk = 0; kk < Cfg::kKSteps; ++kk) {
                             const uint32_t off = kk * 32;
                             const uint32_t acc =
-                                ((!Cfg::kComp && ks > ks0) || a > 0 || kk > 0) ? 1u : 0u;
+                                ((Cfg::kComp ? !g_first : ks > ks0) || a > 0 || kk > 0) ? 1u : 0u;
                             const uint32_t ph = base + a * Cfg::kPBytes + off;
                             const uint32_t qh = qbase + a * Cfg::kQBytes + off;
                             mma<KIND>(d, smem_desc(ph), smem_desc(qh), Cfg::kIdesc, acc);
@@ -461,7 +468,12 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                         }
                     }
                     mma_commit(&empty_bar[s]);
-                    if constexpr (Cfg::kComp) mma_commit(&acc_full[b]);
+                    if constexpr (Cfg::kComp) {
+                        if (g_last) {
+                            mma_commit(&acc_full[b]);
+                            ++grp;
+                        }
+                    }
                 }
                 if (!ok) break;
                 if constexpr (!Cfg::kComp) mma_commit(&acc_full[b]);
@@ -472,7 +484,7 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
         }
     } else {
         // Epilogue warps 0-3: warp w owns TMEM lanes (tile rows) 32w .. 32w+31.
-        int seg = 0, it = 0;
+        int seg = 0, it = 0, grp = 0;
         bool fix_used = false;          // fix_bar serves one staged fix-up
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         // One accumulator is complete (bounded wait by one thread, in warp 2:
@@ -505,8 +517,11 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
 #pragma unroll
                 for (int i = 0; i < N; ++i) sum[i] = cor[i] = 0.0f;
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
-                    const int b = it % kNumAcc;
-                    if (!acc_ready(b, (it / kNumAcc) & 1, false)) {
+                    if (!((ks - ks0) % Cfg::kGroup == Cfg::kGroup - 1 || ks == ks1 - 1)) continue;
+                    const int b = grp % kNumAcc;
+                    const uint32_t par = (grp / kNumAcc) & 1;
+                    ++grp;
+                    if (!acc_ready(b, par, false)) {
                         seg_ok = false;
                         break;
                     }
