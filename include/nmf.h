@@ -254,6 +254,15 @@ nmf_status nmf_batch_create(nmf_batch **out, int32_t count, const nmf_matrix *Xs
                             const int32_t *ranks, const float *const *W0,
                             const float *const *H0, int32_t factors_on_device,
                             const nmf_params *p, void *stream);
+/* As nmf_batch_create, but instance i runs with its own parameters
+ * params[i] (count entries; e.g. the grid of hp, beta0, eta, gamma and
+ * gamma_bar values of the paper's sensitivity study, Sec. 4.2, run on the
+ * same data in one graph).  params is borrowed during the call;
+ * NMF_EINVAL when it is NULL, otherwise errors as nmf_batch_create. */
+nmf_status nmf_batch_create_params(nmf_batch **out, int32_t count, const nmf_matrix *Xs,
+                                   const int32_t *ranks, const float *const *W0,
+                                   const float *const *H0, int32_t factors_on_device,
+                                   const nmf_params *params, void *stream);
 /* `iters` outer iterations of every instance: one graph launch each. */
 nmf_status nmf_batch_step(nmf_batch *b, int32_t iters);
 /* The same iterations as a per-instance launch loop (each instance's own

@@ -1195,9 +1195,13 @@ nmf_status autotune(nmf_batch *b) {
 
 extern "C" {
 
-nmf_status nmf_batch_create(nmf_batch **out, int32_t count, const nmf_matrix *Xs,
-                            const int32_t *ranks, const float *const *W0, const float *const *H0,
-                            int32_t factors_on_device, const nmf_params *p, void *stream) {
+namespace {
+
+// Instance i takes parameters p[i * p_stride] (p_stride 0: one set for all).
+nmf_status batch_create(nmf_batch **out, int32_t count, const nmf_matrix *Xs,
+                        const int32_t *ranks, const float *const *W0, const float *const *H0,
+                        int32_t factors_on_device, const nmf_params *p, size_t p_stride,
+                        void *stream) {
     if (!out) return fail(NMF_EINVAL, "out pointer is NULL");
     *out = nullptr;
     if (count < 1 || !Xs || !ranks || !W0 || !H0)
@@ -1207,7 +1211,8 @@ nmf_status nmf_batch_create(nmf_batch **out, int32_t count, const nmf_matrix *Xs
     b->st = static_cast<cudaStream_t>(stream);
     for (int32_t i = 0; i < count; ++i) {
         nmf_handle *h = nullptr;
-        nmf_status s = nmf_create(&h, &Xs[i], ranks[i], W0[i], H0[i], factors_on_device, p, stream);
+        const nmf_params *pi = p ? p + (size_t)i * p_stride : nullptr;
+        nmf_status s = nmf_create(&h, &Xs[i], ranks[i], W0[i], H0[i], factors_on_device, pi, stream);
         if (s != NMF_OK) {
             free_batch(b);
             char msg[600];
@@ -1232,6 +1237,22 @@ nmf_status nmf_batch_create(nmf_batch **out, int32_t count, const nmf_matrix *Xs
     }
     *out = b;
     return NMF_OK;
+}
+
+}  // namespace
+
+nmf_status nmf_batch_create(nmf_batch **out, int32_t count, const nmf_matrix *Xs,
+                            const int32_t *ranks, const float *const *W0, const float *const *H0,
+                            int32_t factors_on_device, const nmf_params *p, void *stream) {
+    return batch_create(out, count, Xs, ranks, W0, H0, factors_on_device, p, 0, stream);
+}
+
+nmf_status nmf_batch_create_params(nmf_batch **out, int32_t count, const nmf_matrix *Xs,
+                                   const int32_t *ranks, const float *const *W0,
+                                   const float *const *H0, int32_t factors_on_device,
+                                   const nmf_params *params, void *stream) {
+    if (!params) return fail(NMF_EINVAL, "nmf_batch_create_params: params (count entries) is NULL");
+    return batch_create(out, count, Xs, ranks, W0, H0, factors_on_device, params, 1, stream);
 }
 
 nmf_status nmf_batch_step(nmf_batch *b, int32_t iters) {

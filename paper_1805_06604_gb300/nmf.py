@@ -88,6 +88,9 @@ _SIGS = {
     "nmf_batch_create": [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_void_p, ct.c_void_p,
                          ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(nmf_params),
                          ct.c_void_p],
+    "nmf_batch_create_params": [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_void_p, ct.c_void_p,
+                                ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p,
+                                ct.c_void_p],
     "nmf_batch_step": [ct.c_void_p, ct.c_int32],
     "nmf_batch_step_loop": [ct.c_void_p, ct.c_int32],
     "nmf_batch_get_info": [ct.c_void_p, ct.c_int32, ct.POINTER(nmf_info)],
@@ -334,10 +337,19 @@ def nmf_destroy(h):
 class Batch:
     """Many independent instances (host numpy inputs): one graph per iteration."""
 
-    def __init__(self, problems, stream=None, **params):
-        """problems: list of (X m x n float32, r, W0 m x r, H0 r x n)."""
+    def __init__(self, problems, stream=None, per_instance=None, **params):
+        """problems: list of (X m x n float32, r, W0 m x r, H0 r x n).
+        per_instance: optional list (one dict per problem) of parameter
+        overrides applied on top of **params (nmf_batch_create_params)."""
         self.params = nmf_params_default(**params)
         n = len(problems)
+        plist = None
+        if per_instance is not None:
+            if len(per_instance) != n:
+                raise ValueError("per_instance needs one entry per problem")
+            plist = (nmf_params * n)()
+            for i, over in enumerate(per_instance):
+                plist[i] = nmf_params_default(**{**params, **over})
         mats = (nmf_matrix * n)()
         self._keep = []
         ranks = (ct.c_int32 * n)()
@@ -355,9 +367,15 @@ class Batch:
             ranks[i] = int(r)
             self.shapes.append((int(X.shape[0]), int(X.shape[1]), int(r)))
         self.h = ct.c_void_p()
-        _check(load().nmf_batch_create(ct.byref(self.h), n, mats, ranks, w0, h0, 0,
-                                       ct.byref(self.params), _stream_ptr(stream)),
-               "nmf_batch_create")
+        if plist is None:
+            _check(load().nmf_batch_create(ct.byref(self.h), n, mats, ranks, w0, h0, 0,
+                                           ct.byref(self.params), _stream_ptr(stream)),
+                   "nmf_batch_create")
+        else:
+            _check(load().nmf_batch_create_params(ct.byref(self.h), n, mats, ranks, w0, h0, 0,
+                                                  ct.cast(plist, ct.c_void_p),
+                                                  _stream_ptr(stream)),
+                   "nmf_batch_create_params")
         self._keep = None
 
     def step(self, iters=1):

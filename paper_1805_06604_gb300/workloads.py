@@ -13,6 +13,8 @@ them with the shapes and structure of Sec. 4.1):
 
 * ``low_rank``     -- X = W0 H0 with U[0,1] factors (the "low-rank synthetic"
   data of Sec. 4.1), optionally with additive Gaussian noise.
+* ``full_rank``    -- X with i.i.d. U[0,1] entries (the "full-rank synthetic"
+  data of Sec. 4.1).
 * ``image_like``   -- columns are nonnegative mixtures of smooth 2-D Gaussian
   blobs on a 112 x 92 pixel grid (the ORL/Umist image size of Table 1).
 * ``document_like``-- a sparse term-document matrix: Zipf term frequencies,
@@ -103,6 +105,17 @@ def low_rank(m: int, n: int, r: int, seed: int = 0, noise: float = 0.0,
     Wi, Hi = init_factors(m, n, r, seed + 1 if init_seed is None else init_seed, dtype)
     return Problem(name, m, n, r, Wi, Hi, X=X,
                    meta={"seed": seed, "noise": noise, "recipe": "W0,H0~U[0,1]; X=max(0,W0H0+noise*sigma*N)"})
+
+
+def full_rank(m: int = 200, n: int = 200, r: int = 20, seed: int = 0, dtype=np.float32,
+              init_seed: int | None = None) -> Problem:
+    """The "full-rank synthetic" data of Sec. 4.1: every entry of X i.i.d.
+    U[0,1] (m = n = 200, r = 20 in the paper); initial W, H ~ U[0,1]."""
+    g = rng(seed)
+    X = g.random((m, n)).astype(dtype)
+    Wi, Hi = init_factors(m, n, r, seed + 1 if init_seed is None else init_seed, dtype)
+    return Problem(f"full_rank_{m}x{n}_r{r}", m, n, r, Wi, Hi, X=X,
+                   meta={"seed": seed, "recipe": "X~U[0,1]"})
 
 
 def oracle_scale(seed: int = 0) -> Problem:
