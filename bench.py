@@ -230,6 +230,18 @@ def other_workloads(nmf, torch, stream):
         doc[name] = {"iters_per_s": 300 / t, "relerr": sv.info().relerr}
         sv.close()
     out["document_like_csr"] = doc
+    # The parameter study of Sec. 4.2 (reduced: one data set, two
+    # initialisations, all 109 variants in batched graphs).
+    from paper_1805_06604_gb300 import sweep
+    study = {}
+    for kind in ("low_rank", "full_rank"):
+        summ, _, secs = sweep.run(kind, datasets=1, inits=2, iters=500)
+        per = summ["per_variant"]
+        study[kind] = {"seconds": secs, "variants": len(per), "runs": summ["runs"],
+                       "iters": 500, "shape": "200x200 r=20",
+                       "mean_E": {v: per[v]["mean_E"] for v in summ["ranking"]},
+                       "ranking": summ["ranking"]}
+    out["parameter_study"] = study
     return out
 
 
