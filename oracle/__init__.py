@@ -84,7 +84,8 @@ def _load():
         "orc_beta_update": (None, [vp, vp, ct.c_int]),
         "orc_eahals_init": (None, [vp, ct.c_int, _DP, _DP, _DP, _DP, vp, vp]),
         "orc_eahals_step": (None, [vp, ct.c_int, ct.c_double, _DP, _DP, _DP, _DP, vp, vp,
-                                   ct.c_int, _DP, _DP, ct.POINTER(ct.c_int)]),
+                                   ct.c_int, _DP, _DP, ct.POINTER(ct.c_int), _DP]),
+        "orc_line_search_beta": (ct.c_double, [vp, ct.c_int, _DP, _DP, _DP]),
         "orc_eahals_run": (None, [vp, ct.c_int, _DP, _DP, _DP, _DP, vp, vp, ct.c_int,
                                   ct.POINTER(ct.c_int8), _DP, _DP, ct.POINTER(ct.c_uint8)]),
         "orc_ahals_run": (None, [vp, ct.c_int, _DP, _DP, ct.c_int, ct.c_int, ct.c_int, _DP]),
@@ -287,18 +288,31 @@ def eahals_init(X, W0, H0, p: Params) -> State:
     return st
 
 
-def eahals_step(X, st: State, p: Params, force: int = -1, fro2_x: float | None = None):
-    """One outer iteration in place on ``st``; returns (e_k, beta_k, accepted)."""
+def eahals_step(X, st: State, p: Params, force: int = -1, fro2_x: float | None = None,
+                line_search: bool = False):
+    """One outer iteration in place on ``st``; returns (e_k, beta_k, accepted),
+    and the line-search step beta* of Sec. 3 as a fourth value when
+    ``line_search``."""
     X = Matrix.from_any(X)
     if fro2_x is None:
         fro2_x = fro2(X)
     sc, pc = st.s.c(), p.c()
-    e, b, acc = ct.c_double(), ct.c_double(), ct.c_int()
+    e, b, acc, bs = ct.c_double(), ct.c_double(), ct.c_int(), ct.c_double()
     _load().orc_eahals_step(X.ref, st.W.shape[1], float(fro2_x), _ptr(st.W), _ptr(st.H),
                             _ptr(st.Wy), _ptr(st.Hy), ct.byref(pc), ct.byref(sc), int(force),
-                            ct.byref(e), ct.byref(b), ct.byref(acc))
+                            ct.byref(e), ct.byref(b), ct.byref(acc),
+                            ct.byref(bs) if line_search else None)
     st.s.load(sc)
+    if line_search:
+        return e.value, b.value, bool(acc.value), bs.value
     return e.value, b.value, bool(acc.value)
+
+
+def line_search_beta(X, W, Wn, Hy) -> float:
+    """beta* = <X - Wn Hy, (Wn - W) Hy> / ||(Wn - W) Hy||_F^2 (Sec. 3)."""
+    X = Matrix.from_any(X)
+    W, Wn, Hy = _f64(W), _f64(Wn), _f64(Hy)
+    return _load().orc_line_search_beta(X.ref, W.shape[1], _ptr(W), _ptr(Wn), _ptr(Hy))
 
 
 def eahals_run(X, st: State, p: Params, iters: int, forced=None):

@@ -199,6 +199,43 @@ double orc_err2_direct(const orc_matrix *X, int r, const double *W,
     return s;
 }
 
+/* The exact line-search step of Sec. 3 for the W-update: with
+ * W_y(beta) = W_n + beta (W_n - W),
+ *   beta* = <X - W_n H_y, (W_n - W) H_y> / ||(W_n - W) H_y||_F^2,
+ * both inner products formed entry by entry over X (zeros of a CSR X
+ * count).  0 when (W_n - W) H_y = 0. */
+double orc_line_search_beta(const orc_matrix *X, int r, const double *W,
+                            const double *Wn, const double *Hy)
+{
+    const int64_t m = X->m, n = X->n;
+    double *res = orc_alloc(n), *dir = orc_alloc(n);
+    double num = 0.0, den = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            double wh = 0.0, dh = 0.0;
+            for (int k = 0; k < r; ++k) {
+                wh += Wn[i * r + k] * Hy[k * n + j];
+                dh += (Wn[i * r + k] - W[i * r + k]) * Hy[k * n + j];
+            }
+            res[j] = -wh;
+            dir[j] = dh;
+        }
+        if (X->is_csr) {
+            for (int64_t p = X->rowptr[i]; p < X->rowptr[i + 1]; ++p)
+                res[X->colidx[p]] += X->val[p];
+        } else {
+            for (int64_t j = 0; j < n; ++j) res[j] += X->x[i * n + j];
+        }
+        for (int64_t j = 0; j < n; ++j) {
+            num += res[j] * dir[j];
+            den += dir[j] * dir[j];
+        }
+    }
+    free(res);
+    free(dir);
+    return den > 0.0 ? num / den : 0.0;
+}
+
 void orc_sweep_counts(int64_t m, int64_t n, int64_t K, int r, double alpha,
                       int *lw, int *lh)
 {
@@ -254,7 +291,7 @@ void orc_eahals_init(const orc_matrix *X, int r, const double *W,
 void orc_eahals_step(const orc_matrix *X, int r, double fro2, double *W,
                      double *H, double *Wy, double *Hy, const orc_params *p,
                      orc_scalars *s, int force, double *e_out,
-                     double *beta_out, int *accepted_out)
+                     double *beta_out, int *accepted_out, double *beta_star_out)
 {
     const int64_t m = X->m, n = X->n;
     const double beta = s->beta;
@@ -288,6 +325,9 @@ void orc_eahals_step(const orc_matrix *X, int r, double fro2, double *W,
     orc_gram_h(n, r, Hw, D);
     memcpy(Wn, Wy, sizeof(double) * (size_t)(m * r));
     orc_hals_sweeps_w(m, r, C, D, Wn, p->lw);
+
+    /* The line-search step of Sec. 3 for this W-update (a diagnostic). */
+    if (beta_star_out) *beta_star_out = orc_line_search_beta(X, r, W, Wn, Hw);
 
     /* Step 15 via Remark 1, reusing X H_y^T and H_y H_y^T of step 10. */
     double e2 = orc_err2_expanded(fro2, m, r, Wn, C, D);
@@ -336,7 +376,7 @@ void orc_eahals_run(const orc_matrix *X, int r, double *W, double *H,
         double e, b;
         int acc;
         orc_eahals_step(X, r, fro2, W, H, Wy, Hy, p, s,
-                        forced ? forced[it] : -1, &e, &b, &acc);
+                        forced ? forced[it] : -1, &e, &b, &acc, NULL);
         if (trace_e) trace_e[it] = e;
         if (trace_beta) trace_beta[it] = b;
         if (trace_acc) trace_acc[it] = (uint8_t)acc;

@@ -118,11 +118,20 @@ void orc_eahals_init(const orc_matrix *X, int r, const double *W,
 /* One outer iteration of Algorithm 2 (steps 3-20) with Algorithm 3.
  * State (W, H, Wy, Hy, *s) is updated in place.  `force` < 0 lets the
  * error test decide; 0 / 1 forces restart / accept (decision replay).
- * Outputs e(k), the beta used, and the decision.  fro2 = ||X||_F^2. */
+ * Outputs e(k), the beta used, the decision and (when beta_star_out is
+ * not NULL) the line-search step of Sec. 3 for this iteration's W-update
+ * (orc_line_search_beta of W, W_n and the H_y the W-update used).
+ * fro2 = ||X||_F^2. */
 void orc_eahals_step(const orc_matrix *X, int r, double fro2, double *W,
                      double *H, double *Wy, double *Hy, const orc_params *p,
                      orc_scalars *s, int force, double *e_out,
-                     double *beta_out, int *accepted_out);
+                     double *beta_out, int *accepted_out, double *beta_star_out);
+
+/* Sec. 3: beta* = argmin_beta ||X - (W_n + beta (W_n - W)) H_y||_F^2
+ *       = <X - W_n H_y, (W_n - W) H_y> / ||(W_n - W) H_y||_F^2,
+ * evaluated entry by entry (O(mnr)); 0 when (W_n - W) H_y = 0. */
+double orc_line_search_beta(const orc_matrix *X, int r, const double *W,
+                            const double *Wn, const double *Hy);
 
 /* `iters` outer iterations; traces (length iters) may be NULL. */
 void orc_eahals_run(const orc_matrix *X, int r, double *W, double *H,

@@ -10,6 +10,9 @@ Which pin covers which oracle routine:
                                            (all 2^r active sets), monotone decrease
   orc_err2_expanded / orc_err2_direct      Remark 1 identity + numpy direct error
   orc_sweep_counts                         hand-evaluated budgets
+  orc_line_search_beta                     vertex of the parabola through three
+                                           direct errors (Sec. 3), zero cases,
+                                           the step's own W, W_n, H_y
   orc_beta_update                          hand-derived Algorithm 3 sequences
   orc_eahals_*                             hand-worked 2x2 example, beta0 = 0
                                            reduces to A-HALS, accepted errors
@@ -416,3 +419,56 @@ def test_tie_is_accepted():
     np.testing.assert_array_equal(te, [0.0, 0.0, 0.0])
     assert ta.all()
     np.testing.assert_allclose(tb, [0.5, 0.505, 0.51005], rtol=1e-15)
+
+
+# ------------------------------------------------- line-search step (Sec. 3)
+
+def _f_direct(X, W, H):
+    return O.err2_direct(X, W, H)
+
+
+@pytest.mark.parametrize("csr", [False, True])
+def test_line_search_beta_is_the_parabola_vertex(csr):
+    """f(beta) = ||X - (W_n + beta (W_n - W)) H_y||^2 is a quadratic; its
+    vertex from f(-1), f(0), f(1) (direct errors, no shared formula) is
+    beta*, and nearby betas do no better."""
+    m, n, r = 23, 17, 4
+    Xd = _sparse_dense(m, n, 0.4, 41) if csr else _rand((m, n), 41)
+    X = _csr(Xd) if csr else Xd
+    W, Wn, Hy = _rand((m, r), 42), _rand((m, r), 43), _rand((r, n), 44)
+    D = Wn - W
+    f = {b: _f_direct(X, Wn + b * D, Hy) for b in (-1.0, 0.0, 1.0)}
+    vertex = (f[-1.0] - f[1.0]) / (2.0 * (f[-1.0] - 2.0 * f[0.0] + f[1.0]))
+    bs = O.line_search_beta(X, W, Wn, Hy)
+    assert bs == pytest.approx(vertex, rel=1e-9, abs=1e-12)
+    fb = _f_direct(X, Wn + bs * D, Hy)
+    for eps in (1e-2, -1e-2):
+        assert fb <= _f_direct(X, Wn + (bs + eps) * D, Hy)
+
+
+def test_line_search_beta_zero_cases():
+    """No direction (W_n = W) gives 0; an exact fit X = W_n H_y gives 0
+    whatever W (the residual is zero)."""
+    m, n, r = 12, 9, 3
+    W, Wn, Hy = _rand((m, r), 51), _rand((m, r), 52), _rand((r, n), 53)
+    X = Wn @ Hy
+    assert O.line_search_beta(X, W, Wn, Hy) == pytest.approx(0.0, abs=1e-12)
+    assert O.line_search_beta(_rand((m, n), 54), Wn, Wn, Hy) == 0.0
+
+
+def test_step_line_search_uses_the_iterations_w_wn_hy():
+    """hp = 1: the W-update uses H_n, and an accepted step returns W_n, H_n
+    as the new W, H; the step's beta* must equal the formula on (the W
+    before the step, W_n, H_n)."""
+    P = wl.low_rank(30, 25, 4, seed=19, noise=0.05, dtype=np.float64)
+    p = O.Params(hp=1, lw=2, lh=2)
+    st = O.eahals_init(P.X, P.W0, P.H0, p)
+    seen = 0
+    for _ in range(8):
+        W_before = st.W.copy()
+        _, _, acc, bs = O.eahals_step(P.X, st, p, line_search=True)
+        if acc:
+            assert bs == pytest.approx(O.line_search_beta(P.X, W_before, st.W, st.H),
+                                       rel=1e-12, abs=1e-15)
+            seen += 1
+    assert seen >= 3
