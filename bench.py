@@ -242,6 +242,19 @@ def other_workloads(nmf, torch, stream):
                        "mean_E": {v: per[v]["mean_E"] for v in summ["ranking"]},
                        "ranking": summ["ranking"]}
     out["parameter_study"] = study
+    # Sec. 3's line-search step beta* of every W-update (diagnostic trace) on
+    # the low-rank synthetic data: the paper observes it near zero for most
+    # iterations once near a stationary point.
+    P = wl.low_rank(200, 200, 20, seed=1000)
+    sv = nmf.Solver(P.X, P.r, P.W0, P.H0, line_search_trace=1)
+    sv.step(500)
+    bs = np.abs(sv.line_search_trace())
+    sv.close()
+    tail = bs[100:]
+    out["line_search_beta_star"] = {"workload": "low_rank_200x200_r20", "iters": 500,
+                                    "median_abs_after_100": float(np.median(tail)),
+                                    "frac_abs_below_0.1_after_100": float(np.mean(tail < 0.1)),
+                                    "median_abs_first_10": float(np.median(bs[:10]))}
     return out
 
 

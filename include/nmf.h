@@ -88,6 +88,10 @@ typedef struct {
                                 exceeds e(k-1) as computed                      */
     int32_t precision;       /* nmf_precision (NMF_PREC_FP32)                 */
     int64_t trace_capacity;  /* initial device trace length (0 = 4096); grows */
+    int32_t line_search_trace; /* 1: also record, every iteration, the exact
+                                line-search step beta* of Sec. 3 for the
+                                W-update (a diagnostic: one more r x r product
+                                per row of W; nmf_get_line_search_trace); 0  */
 } nmf_params;
 
 typedef struct {
@@ -170,6 +174,19 @@ nmf_status nmf_get_extrapolated(nmf_handle *h, float *Wy, float *Hy,
  * Any of the three pointers may be NULL.  *len receives min(k, cap). */
 nmf_status nmf_get_trace(nmf_handle *h, double *e, double *beta,
                          uint8_t *accepted, int64_t cap, int64_t *len);
+
+/* Sec. 3: beta*(k) = <X - W_n H_y, (W_n - W) H_y> / ||(W_n - W) H_y||_F^2,
+ * the step that minimises ||X - (W_n + beta (W_n - W)) H_y||_F over beta
+ * for iteration k's W-update (W the accepted iterate before it, W_n its
+ * result, H_y the H it used), 0 when (W_n - W) H_y = 0.  Evaluated on the
+ * device without another pass over X: the numerator is
+ * -<W_n D - C, W_n - W> and the denominator sum_i (W_n - W)_i D
+ * (W_n - W)_i^T with C = X H_y^T and D = H_y H_y^T of that iteration.
+ * Copies min(iterations done, cap) values to host beta_star[]; *len gets
+ * the count.  NMF_ENOTSUP unless the handle was created with
+ * line_search_trace = 1. */
+nmf_status nmf_get_line_search_trace(nmf_handle *h, double *beta_star, int64_t cap,
+                                     int64_t *len);
 
 /* Full solver state for checkpoint/resume and for replaying a step from an
  * identical state.  The four factor arrays are host or device per

@@ -107,6 +107,7 @@ struct nmf_handle {
     int *flag = nullptr;
     // trace
     double *tr_e = nullptr, *tr_beta = nullptr;
+    double *tr_bstar = nullptr;                  // line-search diagnostic (optional)
     unsigned char *tr_acc = nullptr;
     int64_t tr_cap = 0;
     int64_t k_enq = 0;                           // iterations enqueued so far
@@ -131,7 +132,7 @@ void free_handle(nmf_handle *h) {
                     h->C_lo, h->D_lo, h->Wt, h->Wq, h->Hq, h->Pc, h->Pc_lo, h->Pa, h->Pa_lo, h->Wth,
                     h->Wtl, h->Hh, h->Hl, h->tct_c, h->tct_a, h->tc_err,
                     h->fro2, h->state, h->partials, h->counter, h->tickets, h->xtickets, h->ws, h->flag,
-                    h->tr_e, h->tr_beta, h->tr_acc};
+                    h->tr_e, h->tr_beta, h->tr_acc, h->tr_bstar};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->h_state) cudaFreeHost(h->h_state);
@@ -306,6 +307,8 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
     wep.trace.beta = h->tr_beta;
     wep.trace.acc = h->tr_acc;
     wep.trace.cap = h->tr_cap;
+    wep.trace.bstar = h->tr_bstar;
+    wep.W_prev = h->p.line_search_trace ? h->W : nullptr;
     NMF_STEP(launch_hals_w(h->m, h->r, h->rs, h->C, h->D, h->Wy, h->Wn, h->lw, wep, st));
     NMF_STEP(mark(NMF_PHASE_FINALIZE));
     NMF_STEP(launch_finalize(h->m, h->rs, h->r, h->ld, h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn,
@@ -339,27 +342,34 @@ nmf_status build_graph(nmf_handle *h) {
 nmf_status ensure_trace(nmf_handle *h, int64_t need) {
     if (need <= h->tr_cap) return NMF_OK;
     int64_t cap = std::max<int64_t>(need, 2 * h->tr_cap);
-    double *e = nullptr, *b = nullptr;
+    double *e = nullptr, *b = nullptr, *bs = nullptr;
     unsigned char *a = nullptr;
     NMF_CUDA(cudaStreamSynchronize(h->st));
     if (dalloc(&e, cap) != cudaSuccess || dalloc(&b, cap) != cudaSuccess ||
-        dalloc(&a, cap) != cudaSuccess) {
+        dalloc(&a, cap) != cudaSuccess ||
+        (h->p.line_search_trace && dalloc(&bs, cap) != cudaSuccess)) {
         cudaFree(e);
         cudaFree(b);
         cudaFree(a);
+        cudaFree(bs);
         return fail(NMF_ENOMEM, "trace allocation of %lld entries failed", (long long)cap);
     }
     if (h->tr_cap > 0) {
         NMF_CUDA(cudaMemcpy(e, h->tr_e, sizeof(double) * h->tr_cap, cudaMemcpyDeviceToDevice));
         NMF_CUDA(cudaMemcpy(b, h->tr_beta, sizeof(double) * h->tr_cap, cudaMemcpyDeviceToDevice));
         NMF_CUDA(cudaMemcpy(a, h->tr_acc, h->tr_cap, cudaMemcpyDeviceToDevice));
+        if (bs)
+            NMF_CUDA(cudaMemcpy(bs, h->tr_bstar, sizeof(double) * h->tr_cap,
+                                cudaMemcpyDeviceToDevice));
     }
     cudaFree(h->tr_e);
     cudaFree(h->tr_beta);
     cudaFree(h->tr_acc);
+    cudaFree(h->tr_bstar);
     h->tr_e = e;
     h->tr_beta = b;
     h->tr_acc = a;
+    h->tr_bstar = bs;
     h->tr_cap = cap;
     return build_graph(h);
 }
@@ -373,6 +383,8 @@ cudaMemcpyKind kind_of(int src_dev, int dst_dev) {
 
 nmf_status check_params(const nmf_params *p) {
     if (p->hp < 1 || p->hp > 3) return fail(NMF_EINVAL, "hp must be 1, 2 or 3 (got %d)", p->hp);
+    if (p->line_search_trace != 0 && p->line_search_trace != 1)
+        return fail(NMF_EINVAL, "line_search_trace must be 0 or 1 (got %d)", p->line_search_trace);
     if (!(p->beta0 >= 0.0 && p->beta0 <= 1.0))
         return fail(NMF_EINVAL, "beta0 must lie in [0, 1] (got %g)", p->beta0);
     if (!(1.0 < p->gamma_bar && p->gamma_bar < p->gamma && p->gamma < p->eta))
@@ -455,6 +467,7 @@ nmf_status nmf_params_default(nmf_params *p) {
     p->compare_prev = 0;
     p->precision = NMF_PREC_FP32;
     p->trace_capacity = 4096;
+    p->line_search_trace = 0;
     return NMF_OK;
 }
 
@@ -839,6 +852,20 @@ nmf_status nmf_get_trace(nmf_handle *h, double *e, double *beta, uint8_t *accept
         if (beta) NMF_CUDA(cudaMemcpy(beta, h->tr_beta, sizeof(double) * n, cudaMemcpyDeviceToHost));
         if (accepted) NMF_CUDA(cudaMemcpy(accepted, h->tr_acc, n, cudaMemcpyDeviceToHost));
     }
+    if (len) *len = n;
+    return NMF_OK;
+}
+
+nmf_status nmf_get_line_search_trace(nmf_handle *h, double *beta_star, int64_t cap, int64_t *len) {
+    if (!h || cap < 0) return fail(NMF_EINVAL, "bad arguments");
+    if (!h->p.line_search_trace)
+        return fail(NMF_ENOTSUP, "the handle was created without line_search_trace = 1");
+    nmf_info info;
+    nmf_status s = nmf_get_info(h, &info);
+    if (s != NMF_OK) return s;
+    int64_t n = std::min<int64_t>(std::min<int64_t>(info.k, h->tr_cap), cap);
+    if (n > 0 && beta_star)
+        NMF_CUDA(cudaMemcpy(beta_star, h->tr_bstar, sizeof(double) * n, cudaMemcpyDeviceToHost));
     if (len) *len = n;
     return NMF_OK;
 }

@@ -43,6 +43,7 @@ struct DevTrace {
     double *e;
     double *beta;
     unsigned char *acc;
+    double *bstar;        // line-search step of Sec. 3 per iteration, or null
     long long cap;
 };
 
@@ -52,6 +53,8 @@ struct DevTrace {
 struct ErrPartial {
     double cross;
     double quad;
+    double bnum;          // line-search diagnostic: -<W_n D - C, W_n - W>
+    double bden;          //                         <(W_n - W) D, W_n - W>
 };
 
 }  // namespace nmfg
@@ -112,6 +115,7 @@ struct WEpilogue {            // optional fused work after the W sweeps
     DevState *state;          // decision + Algorithm 3, or null
     DevParams params;
     DevTrace trace;
+    const float *W_prev;      // the accepted W (line-search diagnostic), or null
 };
 cudaError_t launch_hals_h(int64_t n, int64_t ldh, int r, int rs, const float *A,
                           const float *G, const float *H_in, float *H_out, int sweeps,

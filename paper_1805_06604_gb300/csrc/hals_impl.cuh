@@ -69,7 +69,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // Algorithm 3 and steps 16-20 of Algorithm 2, run by one thread.
 __device__ void decide_and_update_beta(DevState *s, const DevParams &p, const DevTrace &t,
-                                       double cross, double quad) {
+                                       double cross, double quad, double bnum, double bden) {
     // Remark 1 in residual form: ||X||^2 - <W_n, C> + <W_n, W_n D - C>.
     const double e2 = s->fro2 - cross + quad;
     const double e = sqrt(e2 > 0.0 ? e2 : 0.0);
@@ -82,6 +82,8 @@ __device__ void decide_and_update_beta(DevState *s, const DevParams &p, const De
         t.e[k] = e;
         t.beta[k] = s->beta;
         t.acc[k] = (unsigned char)acc;
+        // Sec. 3's line-search step for this W-update (diagnostic only).
+        if (t.bstar) t.bstar[k] = bden > 0.0 ? bnum / bden : 0.0;
     }
     s->beta_used = s->beta;
     s->e_k = e;
@@ -178,6 +180,7 @@ hals_kernel(int64_t items, int r, int64_t ld,
     float *Band = smem + RP * ROW;               // [RP][16]: G(k,k-1..k-D), 1/G(k,k)
     float *Glo = Band + RP * 16;                 // W side with error terms: low part of D
     __shared__ double red_cross[kThreads / 32], red_quad[kThreads / 32];
+    __shared__ double red_bnum[kThreads / 32], red_bden[kThreads / 32];
     __shared__ bool am_last;
     const bool err_terms = LAYOUT == kRow && wep.partials != nullptr;
     // A programmatically dependent successor (the tensor-core X product)
@@ -407,22 +410,55 @@ hals_kernel(int64_t items, int r, int64_t ld,
                 quad = fma((double)x[s], (double)hi[s] + (double)lo[s], quad);
             }
         }
+        // Line-search diagnostic (Sec. 3): with the direction
+        // dW = W_n - W (W the accepted iterate), beta* = num / den where
+        //   num = <X - W_n H_y, dW H_y> = -<W_n D - C, dW>,
+        //   den = ||dW H_y||^2 = sum_i dW_i D dW_i^T.
+        double bnum = 0.0, bden = 0.0;
+        if (wep.W_prev != nullptr) {
+            float dl[S], dd[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int k = s * T + t;
+                dl[s] = (valid && k < r) ? x[s] - wep.W_prev[elem_index<LAYOUT>(item, k, ld)]
+                                         : 0.0f;
+                bnum = fma(-(double)dl[s], (double)hi[s] + (double)lo[s], bnum);
+                dd[s] = 0.0f;
+            }
+#pragma unroll 1
+            for (int j = 0; j < RP; ++j) {
+                const float dj = __shfl_sync(gmask, dl[j / T], j % T, T);
+                const float *row_hi = Grow + j * ROW + t * SP;
+#pragma unroll
+                for (int s = 0; s < S; ++s) dd[s] = fmaf(row_hi[s], dj, dd[s]);
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) bden = fma((double)dl[s], (double)dd[s], bden);
+        }
         cross = warp_sum_d(cross);
         quad = warp_sum_d(quad);
+        bnum = warp_sum_d(bnum);
+        bden = warp_sum_d(bden);
         const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
         if (lane == 0) {
             red_cross[warp] = cross;
             red_quad[warp] = quad;
+            red_bnum[warp] = bnum;
+            red_bden[warp] = bden;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double c = 0.0, qd = 0.0;
+            double c = 0.0, qd = 0.0, bn = 0.0, bd = 0.0;
             for (int w = 0; w < (int)blockDim.x / 32; ++w) {
                 c += red_cross[w];
                 qd += red_quad[w];
+                bn += red_bnum[w];
+                bd += red_bden[w];
             }
             wep.partials[blockIdx.x].cross = c;
             wep.partials[blockIdx.x].quad = qd;
+            wep.partials[blockIdx.x].bnum = bn;
+            wep.partials[blockIdx.x].bden = bd;
             __threadfence();
             const unsigned int done = atomicAdd(wep.counter, 1u);
             am_last = (done == gridDim.x - 1);
@@ -431,28 +467,36 @@ hals_kernel(int64_t items, int r, int64_t ld,
         if (am_last) {
             // Fixed-order sum of the CTA partials (deterministic).
             __threadfence();
-            double c = 0.0, qd = 0.0;
+            double c = 0.0, qd = 0.0, bn = 0.0, bd = 0.0;
             for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
                 const volatile ErrPartial *pp = wep.partials + b;
                 c += pp->cross;
                 qd += pp->quad;
+                bn += pp->bnum;
+                bd += pp->bden;
             }
             c = warp_sum_d(c);
             qd = warp_sum_d(qd);
+            bn = warp_sum_d(bn);
+            bd = warp_sum_d(bd);
             if (lane == 0) {
                 red_cross[warp] = c;
                 red_quad[warp] = qd;
+                red_bnum[warp] = bn;
+                red_bden[warp] = bd;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
-                double cs = 0.0, qs = 0.0;
+                double cs = 0.0, qs = 0.0, bns = 0.0, bds = 0.0;
                 for (int w = 0; w < (int)blockDim.x / 32; ++w) {
                     cs += red_cross[w];
                     qs += red_quad[w];
+                    bns += red_bnum[w];
+                    bds += red_bden[w];
                 }
                 *wep.counter = 0u;
                 if (wep.state != nullptr)
-                    decide_and_update_beta(wep.state, wep.params, wep.trace, cs, qs);
+                    decide_and_update_beta(wep.state, wep.params, wep.trace, cs, qs, bns, bds);
             }
         }
     }

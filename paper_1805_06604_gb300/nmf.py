@@ -40,7 +40,7 @@ class nmf_params(ct.Structure):
                 ("gamma", ct.c_double), ("gamma_bar", ct.c_double), ("lw", ct.c_int32),
                 ("lh", ct.c_int32), ("alpha", ct.c_double), ("project_w", ct.c_int32),
                 ("compare_prev", ct.c_int32), ("precision", ct.c_int32),
-                ("trace_capacity", ct.c_int64)]
+                ("trace_capacity", ct.c_int64), ("line_search_trace", ct.c_int32)]
 
 
 class nmf_info(ct.Structure):
@@ -88,6 +88,7 @@ _SIGS = {
     "nmf_batch_create": [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_void_p, ct.c_void_p,
                          ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(nmf_params),
                          ct.c_void_p],
+    "nmf_get_line_search_trace": [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.POINTER(ct.c_int64)],
     "nmf_batch_create_params": [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_void_p, ct.c_void_p,
                                 ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p,
                                 ct.c_void_p],
@@ -452,6 +453,17 @@ class Solver:
         if cap is None:
             cap = int(self.info().k)
         return nmf_get_trace(self.h, cap)
+
+    def line_search_trace(self, cap=None):
+        """beta* of Sec. 3 for every iteration's W-update (needs
+        line_search_trace=1 at creation)."""
+        if cap is None:
+            cap = int(self.info().k)
+        out = np.zeros(cap)
+        ln = ct.c_int64()
+        _check(load().nmf_get_line_search_trace(self.h, out.ctypes.data, cap, ct.byref(ln)),
+               "nmf_get_line_search_trace")
+        return out[:ln.value]
 
     def get_state(self):
         W = np.zeros((self.m, self.r), np.float32)

@@ -304,3 +304,48 @@ def test_profile_phases_advances_like_step():
         b.step(4)
         assert set(ms) == set(nmf.PHASES) and all(v > 0 for v in ms.values())
         np.testing.assert_array_equal(a.factors()[0], b.factors()[0])
+
+
+@pytest.mark.parametrize("m,n,r,hp,warm,csr", [(300, 220, 12, 3, 3, False),
+                                              (257, 193, 20, 1, 5, False),
+                                              (0, 0, 0, 3, 4, True)])
+def test_line_search_diagnostic_matches_oracle(m, n, r, hp, warm, csr):
+    """beta* of Sec. 3 (line_search_trace = 1), one accepted step from an
+    identical state.  Against the oracle's formula at the GPU's own W_n and
+    H_y: within 1e-5 (1 + |beta*|) -- the device evaluates the numerator
+    -<W_n D - C, W_n - W> from C + C_lo and D + D_lo, and the only other
+    input difference is the FP32 rounding of H_y (~6e-8 relative), worth
+    ~6e-8 ||X|| / ||(W_n - W) H_y|| in beta* (measured: <= 3.3e-8).  Against
+    the full FP64 oracle step (its own W_n, H_y): within 1e-3, the FP32 /
+    FP64 sweeps' W_n differing by up to ~1e-5 ||W|| against
+    ||W_n - W|| ~ 1e-2 ||W|| (measured: <= 4e-7)."""
+    from gpu_helpers import load_state, state_to_f32
+    if csr:
+        P = _document()
+    else:
+        P = wl.low_rank(m, n, r, seed=13, noise=0.05)
+    p = oracle_params(P, hp=hp)
+    Xo = oracle_X(P)
+    st = O.eahals_init(Xo, P.W0.astype(np.float32), P.H0.astype(np.float32), p)
+    O.eahals_run(Xo, st, p, warm)
+    st = state_to_f32(st)
+    W0, H0, beta = st.W.copy(), st.H.copy(), st.s.beta
+    with make_solver(P, p, line_search_trace=1) as s:
+        load_state(s, st)
+        s.step(1)
+        _, W, H, _, _ = s.get_state()
+        acc = bool(s.trace()[2][-1])
+        bs_gpu = s.line_search_trace()[-1]
+        with pytest.raises(nmf.NmfError):
+            with make_solver(P, p) as s2:      # not enabled: NMF_ENOTSUP
+                s2.line_search_trace(1)
+    _, _, acc_o, bs_orc = O.eahals_step(Xo, st, p, line_search=True)
+    assert acc and acc_o
+    Wn, Hn = W.astype(np.float64), H.astype(np.float64)
+    Hy = Hn if hp == 1 else Hn + beta * (Hn - H0)
+    if hp == 3:
+        Hy = np.maximum(Hy, 0.0)
+    bs_mixed = O.line_search_beta(Xo, W0, Wn, Hy)
+    print(f"\nbeta*: gpu {bs_gpu:.9f} oracle-at-gpu-iterates {bs_mixed:.9f} oracle {bs_orc:.9f}")
+    assert abs(bs_gpu - bs_mixed) <= 1e-5 * (1.0 + abs(bs_mixed))
+    assert abs(bs_gpu - bs_orc) <= 1e-3
