@@ -116,3 +116,16 @@ def test_parameter_study_runs_and_ranks():
     best = min(per[summ["best"][h]]["mean_E"] for h in summ["best"])
     assert best < per[sweep.AHALS]["mean_E"]
     assert all(sum(r) == summ["runs"] for r in summ["ranking"].values())
+
+
+def test_per_instance_parameters_are_validated():
+    """A bad parameter set in one instance fails the whole batch with that
+    instance's index in the message; params = NULL is rejected."""
+    import ctypes as ct
+    P = wl.low_rank(50, 40, 4, seed=6)
+    with pytest.raises(nmf.NmfError) as ei:
+        nmf.Batch([(P.X, P.r, P.W0, P.H0)] * 3, per_instance=[{}, {"hp": 5}, {}])
+    assert ei.value.status == nmf.NMF_EINVAL and "instance 1" in str(ei.value)
+    h = ct.c_void_p()
+    st = nmf.load().nmf_batch_create_params(ct.byref(h), 1, None, None, None, None, 0, None, None)
+    assert st == nmf.NMF_EINVAL

@@ -236,6 +236,7 @@ def test_solve_stops_at_target():
 
 
 @pytest.mark.parametrize("case", ["nan_x", "neg_w0", "rank_cap", "bad_hp", "bad_gamma",
+                                  "bad_line_search",
                                   "csr_col", "csr_rowptr"])
 def test_invalid_inputs_are_rejected(case):
     P = wl.low_rank(40, 30, 4, seed=16, noise=0.0)
@@ -260,6 +261,8 @@ def test_invalid_inputs_are_rejected(case):
         kw = dict(hp=4)
     elif case == "bad_gamma":
         kw = dict(gamma=1.001, gamma_bar=1.005)
+    elif case == "bad_line_search":
+        kw = dict(line_search_trace=2)
     else:
         rp, ci, v = wl.csr_from_dense(X)
         ci = ci.copy()
