@@ -360,6 +360,29 @@ def run_reference(args, world, rank):
     return line
 
 
+def rank_max_seconds(t: float, dist, device) -> float:
+    """The slowest rank's timed-region seconds (max over ranks; t itself on
+    one process).  Every rank times its own independent instance."""
+    if dist is None:
+        return t
+    import torch
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_value(world: int, steps: int, t_max: float) -> float:
+    """Iterations per second of the whole job: every rank ran `steps`
+    iterations of its own instance within the slowest rank's time."""
+    return world * steps / t_max
+
+
+def instance_seed(seed: int, rank: int) -> int:
+    """Each rank solves a different instance (weak scaling, no collective
+    on the data path)."""
+    return seed + rank
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -378,7 +401,7 @@ def run_ours(args, world, rank, local):
         if dist is not None:
             dist.barrier()
 
-    P = make_workload(args.seed + rank)
+    P = make_workload(instance_seed(args.seed, rank))
     lw, lh = nmf.nmf_sweep_counts(P.m, P.n, P.nnz, P.r)
     stream = torch.cuda.current_stream()
     Xd = torch.from_numpy(P.X).cuda()
@@ -401,13 +424,9 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    t = e0.elapsed_time(e1) / 1000.0
-    if dist is not None:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = rank_max_seconds(e0.elapsed_time(e1) / 1000.0, dist, "cuda")
     info = solver.info()
-    value = world * args.steps / t
+    value = whole_job_value(world, args.steps, t)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
