@@ -16,16 +16,17 @@ namespace {
 constexpr int kSlots4[] = {17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32};
 constexpr int kSlots2[] = {2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 15, 16, 17,
                            18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32};
-// Threads per CTA of a sweep launch.  128 (one warp per scheduler of an
-// SM) unless the warps number between one and two per scheduler of the GPU:
-// there 128-thread CTAs leave a few SMs with twice the work of the rest,
-// and 64-thread CTAs spread it more evenly (dense 10000 x 4000 r = 50,
-// W side: 180 us against 200 us; the H side and the small and sparse
-// problems measured best at 128).
+// Threads per CTA of a sweep launch.  Between ~0.4 and two warps per
+// scheduler of the GPU, 96-thread CTAs (three warps) spread the warps over
+// more SMs than 128-thread ones and leave fewer SMs with a double share than
+// 64-thread ones (dense 10000 x 4000 r = 50: H side 250 warps 342.7 us
+// against 347.5 at 128; W side 625 warps 180.7 us against 184.2 at 64 and
+// 200 at 128).  Outside that range -- the small, batched and sparse
+// problems -- 128 measured best.
 int cta_threads(int64_t items, int T) {
     const int64_t warps = (items * T + 31) / 32;
     const int64_t schedulers = 4LL * kNumSMs;
-    return (warps > schedulers && warps <= 2 * schedulers) ? 64 : 128;
+    return (warps * 5 >= 2 * schedulers && warps <= 2 * schedulers) ? 96 : 128;
 }
 
 template <int N>
