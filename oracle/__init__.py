@@ -38,7 +38,7 @@ class _Params(ct.Structure):
     _fields_ = [("hp", ct.c_int), ("beta0", ct.c_double), ("eta", ct.c_double),
                 ("gamma", ct.c_double), ("gamma_bar", ct.c_double),
                 ("lw", ct.c_int), ("lh", ct.c_int), ("project_w", ct.c_int),
-                ("compare_prev", ct.c_int)]
+                ("compare_prev", ct.c_int), ("nnls_exact", ct.c_int)]
 
 
 class _Scalars(ct.Structure):
@@ -86,6 +86,8 @@ def _load():
         "orc_eahals_step": (None, [vp, ct.c_int, ct.c_double, _DP, _DP, _DP, _DP, vp, vp,
                                    ct.c_int, _DP, _DP, ct.POINTER(ct.c_int), _DP]),
         "orc_line_search_beta": (ct.c_double, [vp, ct.c_int, _DP, _DP, _DP]),
+        "orc_nnls": (ct.c_int, [ct.c_int, _DP, _DP, _DP, ct.c_int]),
+        "orc_nnls_h": (ct.c_int, [ct.c_int64, ct.c_int, _DP, _DP, _DP]),
         "orc_eahals_run": (None, [vp, ct.c_int, _DP, _DP, _DP, _DP, vp, vp, ct.c_int,
                                   ct.POINTER(ct.c_int8), _DP, _DP, ct.POINTER(ct.c_uint8)]),
         "orc_ahals_run": (None, [vp, ct.c_int, _DP, _DP, ct.c_int, ct.c_int, ct.c_int, _DP]),
@@ -156,10 +158,11 @@ class Params:
     lh: int = 1
     project_w: int = 0
     compare_prev: int = 0
+    nnls_exact: int = 0          # 1: ANLS / E-ANLS (exact NNLS subproblems)
 
     def c(self) -> _Params:
         return _Params(self.hp, self.beta0, self.eta, self.gamma, self.gamma_bar,
-                       self.lw, self.lh, self.project_w, self.compare_prev)
+                       self.lw, self.lh, self.project_w, self.compare_prev, self.nnls_exact)
 
 
 @dataclass
@@ -306,6 +309,26 @@ def eahals_step(X, st: State, p: Params, force: int = -1, fro2_x: float | None =
     if line_search:
         return e.value, b.value, bool(acc.value), bs.value
     return e.value, b.value, bool(acc.value)
+
+
+def nnls(G, b, x0=None, max_iter: int | None = None):
+    """Exact min_{x>=0} 1/2 x^T G x - b^T x (block principal pivoting);
+    returns (x, exchanges) -- exchanges is -1 on failure."""
+    G = _f64(G)
+    b = _f64(b)
+    r = b.shape[0]
+    x = np.zeros(r) if x0 is None else _f64(x0).copy()
+    it = _load().orc_nnls(r, _ptr(G), _ptr(b), _ptr(x), 100 * (r + 1) if max_iter is None
+                          else int(max_iter))
+    return x, it
+
+
+def nnls_h(A, G, H):
+    """Every column of H solved exactly (warm start: H); returns (H, worst)."""
+    A, G = _f64(A), _f64(G)
+    H = _f64(H).copy()
+    st = _load().orc_nnls_h(H.shape[1], H.shape[0], _ptr(A), _ptr(G), _ptr(H))
+    return H, st
 
 
 def line_search_beta(X, W, Wn, Hy) -> float:

@@ -158,6 +158,165 @@ void orc_hals_sweeps_w(int64_t m, int r, const double *C, const double *D,
         for (int k = 0; k < r; ++k) orc_hals_col_w(m, r, C, D, W, k);
 }
 
+/* Solves G_FF z = c for the free set F (Cholesky of the |F| x |F| block,
+ * FP64).  F given as a list of nf indices.  Returns 0, or -1 when the block
+ * is not positive definite. */
+static int orc_solve_free(int r, const double *G, const double *c, const int *F, int nf,
+                          double *z)
+{
+    double *L = orc_alloc((int64_t)nf * nf);
+    for (int a = 0; a < nf; ++a) {
+        for (int b = 0; b <= a; ++b) {
+            double v = G[F[a] * r + F[b]];
+            for (int q = 0; q < b; ++q) v -= L[a * nf + q] * L[b * nf + q];
+            if (a == b) {
+                if (!(v > 0.0)) {
+                    free(L);
+                    return -1;
+                }
+                L[a * nf + a] = sqrt(v);
+            } else {
+                L[a * nf + b] = v / L[b * nf + b];
+            }
+        }
+    }
+    for (int a = 0; a < nf; ++a) {           /* L y = c_F */
+        double v = c[F[a]];
+        for (int q = 0; q < a; ++q) v -= L[a * nf + q] * z[q];
+        z[a] = v / L[a * nf + a];
+    }
+    for (int a = nf - 1; a >= 0; --a) {      /* L^T z = y */
+        double v = z[a];
+        for (int q = a + 1; q < nf; ++q) v -= L[q * nf + a] * z[q];
+        z[a] = v / L[a * nf + a];
+    }
+    free(L);
+    return 0;
+}
+
+/* Exact NNLS of the ANLS subproblems (Sec. 1, "solved exactly"):
+ *   min_{x >= 0} 1/2 x^T G x - b^T x,  G = W^T W (r x r), b = W^T v,
+ * i.e. min_{x >= 0} ||v - W x||^2, by block principal pivoting (Kim & Park,
+ * the active-set-like method the paper uses): a free set F and its
+ * complement, x_F = G_FF^{-1} b_F, x = 0 off F, y = G x - b (zero on F);
+ * the infeasible indices {i in F: x_i < 0} and {i not in F: y_i < 0} all
+ * change sides while their number keeps falling, with up to three further
+ * full exchanges allowed, otherwise only the largest such index changes
+ * side.  The KKT point (x >= 0, y >= 0, x_i y_i = 0) is the unique minimiser
+ * when G is positive definite.  Comparisons use a tolerance of 1e-12 times
+ * the scale of b and G (FP64 round-off at a degenerate optimum).  Indices
+ * with G_ii = 0 (a zero column of W: the whole row of G is zero) do not
+ * enter the problem and keep their value in x.  x holds the warm start on
+ * entry (its support is the first free set) and the solution on return.
+ * Returns the number of exchanges, or -1 when max_iter is reached or a free
+ * block is singular (x is then the last iterate). */
+int orc_nnls(int r, const double *G, const double *b, double *x, int max_iter)
+{
+    int *free_ = (int *)calloc((size_t)r, sizeof(int));
+    int *act = (int *)calloc((size_t)r, sizeof(int));   /* index takes part */
+    int *F = (int *)malloc(sizeof(int) * (size_t)(r > 0 ? r : 1));
+    double *z = orc_alloc(r > 0 ? r : 1), *y = orc_alloc(r > 0 ? r : 1);
+    double scale = 0.0;
+    for (int i = 0; i < r; ++i) {
+        act[i] = G[i * r + i] > 0.0;
+        if (act[i]) free_[i] = x[i] > 0.0;
+        if (fabs(b[i]) > scale) scale = fabs(b[i]);
+        if (fabs(G[i * r + i]) > scale) scale = fabs(G[i * r + i]);
+    }
+    const double tol = 1e-12 * (scale > 0.0 ? scale : 1.0);
+    int best = r + 1, alpha = 3, it = 0, status = -1;
+    for (;;) {
+        /* Solve on the free set; y on its complement. */
+        int nf = 0;
+        for (int i = 0; i < r; ++i)
+            if (act[i] && free_[i]) F[nf++] = i;
+        if (orc_solve_free(r, G, b, F, nf, z) != 0) break;
+        for (int i = 0; i < r; ++i)
+            if (act[i]) x[i] = 0.0;
+        for (int a = 0; a < nf; ++a) x[F[a]] = z[a];
+        for (int i = 0; i < r; ++i) {
+            y[i] = 0.0;
+            if (!act[i] || free_[i]) continue;
+            double v = -b[i];
+            for (int a = 0; a < nf; ++a) v += G[i * r + F[a]] * z[a];
+            y[i] = v;
+        }
+        /* Infeasible indices. */
+        int nv = 0, last = -1;
+        for (int i = 0; i < r; ++i) {
+            if (!act[i]) continue;
+            const int bad = free_[i] ? (x[i] < -tol) : (y[i] < -tol);
+            if (bad) {
+                ++nv;
+                last = i;
+            }
+        }
+        if (nv == 0) {
+            status = it;
+            break;
+        }
+        if (it >= max_iter) break;
+        ++it;
+        if (nv < best) {
+            best = nv;
+            alpha = 3;
+        } else if (alpha >= 1) {
+            alpha -= 1;
+        } else {
+            free_[last] = !free_[last];   /* backup rule: the largest index only */
+            continue;
+        }
+        for (int i = 0; i < r; ++i) {
+            if (!act[i]) continue;
+            const int bad = free_[i] ? (x[i] < -tol) : (y[i] < -tol);
+            if (bad) free_[i] = !free_[i];
+        }
+    }
+    /* Clamp the round-off negatives a converged free set may carry. */
+    if (status >= 0)
+        for (int i = 0; i < r; ++i)
+            if (act[i] && x[i] < 0.0) x[i] = 0.0;
+    free(free_);
+    free(act);
+    free(F);
+    free(z);
+    free(y);
+    return status;
+}
+
+/* Exact subproblems of ANLS: every column of H (G = W^T W, b = A[:, j])
+ * and every row of W (G = D, b = C[i, :]), warm-started from the values
+ * held in H and W.  Returns the largest exchange count, -1 on failure. */
+int orc_nnls_h(int64_t n, int r, const double *A, const double *G, double *H)
+{
+    double *b = orc_alloc(r), *x = orc_alloc(r);
+    int worst = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        for (int k = 0; k < r; ++k) {
+            b[k] = A[k * n + j];
+            x[k] = H[k * n + j];
+        }
+        const int st = orc_nnls(r, G, b, x, 100 * (r + 1));
+        if (st < 0) worst = -1;
+        else if (worst >= 0 && st > worst) worst = st;
+        for (int k = 0; k < r; ++k) H[k * n + j] = x[k];
+    }
+    free(b);
+    free(x);
+    return worst;
+}
+
+int orc_nnls_w(int64_t m, int r, const double *C, const double *D, double *W)
+{
+    int worst = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        const int st = orc_nnls(r, D, C + i * r, W + i * r, 100 * (r + 1));
+        if (st < 0) worst = -1;
+        else if (worst >= 0 && st > worst) worst = st;
+    }
+    return worst;
+}
+
 /* Remark 1: ||X||^2 - 2 <W, X H^T> + <W^T W, H H^T>. */
 double orc_err2_expanded(double fro2, int64_t m, int r, const double *W,
                          const double *C, const double *D)
@@ -305,7 +464,8 @@ void orc_eahals_step(const orc_matrix *X, int r, double fro2, double *W,
     orc_wtx(X, r, Wy, A);
     orc_gram_w(m, r, Wy, G);
     memcpy(Hn, Hy, sizeof(double) * (size_t)(r * n));
-    orc_hals_sweeps_h(n, r, A, G, Hn, p->lh);
+    if (p->nnls_exact) orc_nnls_h(n, r, A, G, Hn);     /* E-ANLS: exact */
+    else orc_hals_sweeps_h(n, r, A, G, Hn, p->lh);
 
     /* Steps 4-9: for hp >= 2, H_y = H_n + beta (H_n - H), projected when
      * hp = 3.  For hp = 1 the W-update uses H_n (H is extrapolated only
@@ -324,7 +484,8 @@ void orc_eahals_step(const orc_matrix *X, int r, double fro2, double *W,
     orc_xht(X, r, Hw, C);
     orc_gram_h(n, r, Hw, D);
     memcpy(Wn, Wy, sizeof(double) * (size_t)(m * r));
-    orc_hals_sweeps_w(m, r, C, D, Wn, p->lw);
+    if (p->nnls_exact) orc_nnls_w(m, r, C, D, Wn);
+    else orc_hals_sweeps_w(m, r, C, D, Wn, p->lw);
 
     /* The line-search step of Sec. 3 for this W-update (a diagnostic). */
     if (beta_star_out) *beta_star_out = orc_line_search_beta(X, r, W, Wn, Hw);

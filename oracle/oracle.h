@@ -48,6 +48,9 @@ typedef struct {
     int project_w;            /* 1: W_y = max(0, W_y) after extrapolation */
     int compare_prev;         /* 0: compare e(k) with the last accepted
                                  error; 1: with e(k-1) as computed       */
+    int nnls_exact;           /* 1: solve both NNLS subproblems exactly
+                                 (ANLS, Sec. 1; with extrapolation:
+                                 E-ANLS) instead of lh / lw HALS sweeps  */
 } orc_params;
 
 typedef struct {
@@ -88,6 +91,18 @@ void orc_hals_sweeps_h(int64_t n, int r, const double *A, const double *G,
                        double *H, int sweeps);
 void orc_hals_sweeps_w(int64_t m, int r, const double *C, const double *D,
                        double *W, int sweeps);
+
+/* Exact NNLS, min_{x >= 0} 1/2 x^T G x - b^T x (G = W^T W, b = W^T v), by
+ * block principal pivoting (the active-set-like method of Kim & Park that
+ * the paper uses for ANLS, Sec. 1).  x: warm start in, solution out.
+ * Indices with G_ii = 0 keep their value.  Returns the number of exchanges,
+ * -1 if max_iter is reached or a free block is singular. */
+int orc_nnls(int r, const double *G, const double *b, double *x, int max_iter);
+
+/* ANLS subproblems solved exactly: every column of H (G, A = W^T X) and
+ * every row of W (D, C = X H^T), warm-started from H / W. */
+int orc_nnls_h(int64_t n, int r, const double *A, const double *G, double *H);
+int orc_nnls_w(int64_t m, int r, const double *C, const double *D, double *W);
 
 /* Remark 1: ||X - WH||^2 = ||X||^2 - 2<W, X H^T> + <W^T W, H H^T>,
  * with C = X H^T and D = H H^T given. */
