@@ -70,3 +70,17 @@ def test_create_without_gpu_fails_loudly():
     with pytest.raises(nmf.NmfError) as ei:
         nmf.Solver(X, 2, np.ones((4, 2), np.float32), np.ones((2, 3), np.float32))
     assert ei.value.status == nmf.NMF_ECUDA
+
+
+def test_optional_diagnostics_are_off_by_default(lib):
+    p = nmf.nmf_params_default()
+    assert p.line_search_trace == 0 and p.trace_capacity == 4096
+    assert nmf.nmf_params_default(line_search_trace=1).line_search_trace == 1
+
+
+def test_batch_per_instance_length_is_checked_before_any_device_call(lib):
+    import numpy as np
+    X = np.ones((8, 6), np.float32)
+    W0, H0 = np.ones((8, 2), np.float32), np.ones((2, 6), np.float32)
+    with pytest.raises(ValueError):
+        nmf.Batch([(X, 2, W0, H0)] * 2, per_instance=[{}])
