@@ -572,3 +572,20 @@ def test_eanls_accelerates_anls_on_low_rank(m, n, r, seed, floor):
         O.eahals_run(P.X, st, p, K)
         errs[name] = np.linalg.norm(P.X - st.W @ st.H) / np.linalg.norm(P.X)
     assert errs["eanls"] < floor and errs["anls"] > 1e-3, errs
+
+
+def test_eanls_csr_and_dense_agree_and_hp3_stays_feasible():
+    """E-ANLS on a sparse X: the CSR and dense oracles take the same
+    decisions and reach the same iterates; with hp = 3 every accepted pair
+    and the projected H_y stay nonnegative."""
+    X = _sparse_dense(40, 30, 0.3, 13)
+    W0, H0 = wl.init_factors(40, 30, 4, 14, np.float64)
+    p = O.Params(hp=3, beta0=0.5, eta=1.5, gamma=1.1, gamma_bar=1.05, nnls_exact=1)
+    st1 = O.eahals_init(X, W0, H0, p)
+    st2 = O.eahals_init(_csr(X), W0, H0, p)
+    te1, _, ta1 = O.eahals_run(X, st1, p, 12)
+    te2, _, ta2 = O.eahals_run(_csr(X), st2, p, 12)
+    np.testing.assert_array_equal(ta1, ta2)
+    np.testing.assert_allclose(te1, te2, rtol=1e-10)
+    np.testing.assert_allclose(st1.W, st2.W, rtol=1e-9, atol=1e-12)
+    assert np.all(st1.W >= 0) and np.all(st1.H >= 0) and np.all(st1.Hy >= 0)
