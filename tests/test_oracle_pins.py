@@ -22,6 +22,7 @@ Which pin covers which oracle routine:
                                            reduces to A-HALS, accepted errors
                                            monotone, hp=3 feasibility, exact
                                            power-of-two scaling equivariance,
+                                           row / column permutation equivariance,
                                            low-rank recovery, KKT, acceleration
                                            over A-HALS (Table 3's claim)
 """
@@ -589,3 +590,31 @@ def test_eanls_csr_and_dense_agree_and_hp3_stays_feasible():
     np.testing.assert_allclose(te1, te2, rtol=1e-10)
     np.testing.assert_allclose(st1.W, st2.W, rtol=1e-9, atol=1e-12)
     assert np.all(st1.W >= 0) and np.all(st1.H >= 0) and np.all(st1.Hy >= 0)
+
+
+@pytest.mark.parametrize("side", ["rows", "cols"])
+def test_permutation_equivariance(side):
+    """Permuting the rows of X and W (or the columns of X and H) permutes
+    the iterates: the closed-form updates act per row of W / column of H and
+    the products only sum in another order (agreement to round-off, same
+    decisions)."""
+    P = wl.low_rank(36, 28, 4, seed=17, noise=0.05, dtype=np.float64)
+    perm = wl.rng(18).permutation(P.m if side == "rows" else P.n)
+    X, W0, H0 = P.X, P.W0, P.H0
+    if side == "rows":
+        Xp, W0p, H0p = X[perm], W0[perm], H0
+    else:
+        Xp, W0p, H0p = X[:, perm], W0, H0[:, perm]
+    p = O.Params(hp=3, lw=3, lh=3)
+    st = O.eahals_init(X, W0, H0, p)
+    stp = O.eahals_init(Xp, W0p, H0p, p)
+    te, _, ta = O.eahals_run(X, st, p, 20)
+    tep, _, tap = O.eahals_run(Xp, stp, p, 20)
+    np.testing.assert_array_equal(ta, tap)
+    np.testing.assert_allclose(te, tep, rtol=1e-10)
+    if side == "rows":
+        np.testing.assert_allclose(st.W[perm], stp.W, rtol=1e-8, atol=1e-12)
+        np.testing.assert_allclose(st.H, stp.H, rtol=1e-8, atol=1e-12)
+    else:
+        np.testing.assert_allclose(st.W, stp.W, rtol=1e-8, atol=1e-12)
+        np.testing.assert_allclose(st.H[:, perm], stp.H, rtol=1e-8, atol=1e-12)
