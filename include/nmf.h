@@ -171,7 +171,9 @@ nmf_status nmf_get_extrapolated(nmf_handle *h, float *Wy, float *Hy,
 
 /* Copies the per-iteration trace to host arrays of length `cap`: e(k), the
  * beta_k used by iteration k, and the accept (1) / restart (0) decision.
- * Any of the three pointers may be NULL.  *len receives min(k, cap). */
+ * Any of the three pointers may be NULL.  *len receives min(k, cap).
+ * Entry k is written by iteration k; after nmf_set_state moved k forward,
+ * the entries of iterations this handle did not run are undefined. */
 nmf_status nmf_get_trace(nmf_handle *h, double *e, double *beta,
                          uint8_t *accepted, int64_t cap, int64_t *len);
 
@@ -183,8 +185,9 @@ nmf_status nmf_get_trace(nmf_handle *h, double *e, double *beta,
  * -<W_n D - C, W_n - W> and the denominator sum_i (W_n - W)_i D
  * (W_n - W)_i^T with C = X H_y^T and D = H_y H_y^T of that iteration.
  * Copies min(iterations done, cap) values to host beta_star[]; *len gets
- * the count.  NMF_ENOTSUP unless the handle was created with
- * line_search_trace = 1. */
+ * the count (entries of iterations this handle did not run, after
+ * nmf_set_state, are undefined, as in nmf_get_trace).  NMF_ENOTSUP unless
+ * the handle was created with line_search_trace = 1. */
 nmf_status nmf_get_line_search_trace(nmf_handle *h, double *beta_star, int64_t cap,
                                      int64_t *len);
 
