@@ -83,9 +83,11 @@ typedef struct {
     double alpha;            /* alpha of that budget (0.5)                    */
     int32_t project_w;       /* 1: W_y = max(0, W_y) after extrapolation (the
                                 paper's Algorithm 2 does not project W_y; 0)  */
-    int32_t compare_prev;    /* 0: restart when e(k) exceeds the error of the
-                                last accepted iterate (default); 1: when it
-                                exceeds e(k-1) as computed                      */
+    int32_t compare_prev;    /* 1 (default): restart when e(k) > e(k-1), the
+                                error the previous iteration computed, whether
+                                it was accepted or not (Algorithm 2 step 16 as
+                                written); 0: when e(k) exceeds the error of
+                                the last accepted iterate (an option)          */
     int32_t precision;       /* nmf_precision (NMF_PREC_FP32)                 */
     int64_t trace_capacity;  /* initial device trace length (0 = 4096); grows */
     int32_t line_search_trace; /* 1: also record, every iteration, the exact

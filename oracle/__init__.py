@@ -157,7 +157,7 @@ class Params:
     lw: int = 1
     lh: int = 1
     project_w: int = 0
-    compare_prev: int = 0
+    compare_prev: int = 1        # 1: restart iff e(k) > e(k-1) (Alg. 2 step 16)
     nnls_exact: int = 0          # 1: ANLS / E-ANLS (exact NNLS subproblems)
 
     def c(self) -> _Params:

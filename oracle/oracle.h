@@ -46,8 +46,11 @@ typedef struct {
     double gamma_bar;         /* Algorithm 3 growth factor of beta_bar   */
     int lw, lh;               /* inner HALS sweeps on W and on H         */
     int project_w;            /* 1: W_y = max(0, W_y) after extrapolation */
-    int compare_prev;         /* 0: compare e(k) with the last accepted
-                                 error; 1: with e(k-1) as computed       */
+    int compare_prev;         /* 1: restart iff e(k) > e(k-1), e(k-1) the
+                                 error the previous iteration computed,
+                                 accepted or not (Alg. 2 step 16 as
+                                 written); 0: iff e(k) exceeds the error
+                                 of the last accepted iterate (option)   */
     int nnls_exact;           /* 1: solve both NNLS subproblems exactly
                                  (ANLS, Sec. 1; with extrapolation:
                                  E-ANLS) instead of lh / lw HALS sweeps  */

@@ -464,7 +464,7 @@ nmf_status nmf_params_default(nmf_params *p) {
     p->lh = 0;
     p->alpha = 0.5;
     p->project_w = 0;
-    p->compare_prev = 0;
+    p->compare_prev = 1;
     p->precision = NMF_PREC_FP32;
     p->trace_capacity = 4096;
     p->line_search_trace = 0;

@@ -18,7 +18,9 @@
 //  * host code cannot use the array's name as a device address, so the
 //    first call on each device looks the address up with
 //    cudaGetSymbolAddress (with that device current) and caches it; make
-//    that first call before any stream capture.
+//    that first call before any stream capture.  The cached address belongs
+//    to the device's current context: after a cudaDeviceReset in the same
+//    process it is stale, so the entry point must not be used after one.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -62,11 +64,20 @@ fro2_partial_noalloc(const float *__restrict__ X, int64_t n, int64_t ld, int64_t
                      double *__restrict__ part) {
     const int64_t base = (int64_t)blockIdx.x * kThreads * kPerThread;
     double acc = 0.0;
-    for (int64_t u = 0; u < kPerThread; ++u) {
-        const int64_t q = base + u * kThreads + threadIdx.x;
-        if (q < count) {
-            const double x = (double)X[(q / n) * ld + q % n];
-            acc = fma(x, x, acc);
+    // Entry q = base + u * kThreads + t sits at row q / n, column q % n; the
+    // position is divided out once per thread and then advanced by kThreads
+    // entries, dividing again only when it wraps into a later row.
+    int64_t q = base + threadIdx.x;
+    int64_t row = q / n, col = q - row * n;
+    for (int64_t u = 0; u < kPerThread && q < count; ++u) {
+        const double x = (double)X[row * ld + col];
+        acc = fma(x, x, acc);
+        q += kThreads;
+        col += kThreads;
+        if (col >= n) {                          // wrapped into a later row
+            const int64_t d = col / n;
+            row += d;
+            col -= d * n;
         }
     }
     const double s = block_sum(acc);
@@ -89,8 +100,8 @@ extern "C" nmf_status nmf_fro2_noalloc(const float *X, int64_t m, int64_t n, int
     if (!X || !out) return nmfg::set_error(NMF_EINVAL, "nmf_fro2_noalloc: X and out are required");
     if (m < 1 || n < 1 || ld < n)
         return nmfg::set_error(NMF_EINVAL, "nmf_fro2_noalloc: need m, n >= 1 and ld >= n");
-    const int64_t count = m * n;
-    if (count > kMaxCount)
+    // Compare before multiplying: m * n itself could overflow int64.
+    if (n > kMaxCount / m)
         return nmfg::set_error(NMF_ENOTSUP,
                                "nmf_fro2_noalloc: m*n exceeds 2^28 entries, the capacity of its "
                                "fixed 128 KiB scratch");
@@ -111,6 +122,7 @@ extern "C" nmf_status nmf_fro2_noalloc(const float *X, int64_t m, int64_t n, int
         scratch = g_scratch_ptr[dev];
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t count = m * n;
     const int parts = (int)((count + kThreads * kPerThread - 1) / (kThreads * kPerThread));
     fro2_partial_noalloc<<<parts, kThreads, 0, st>>>(X, n, ld, count, scratch);
     e = cudaGetLastError();

@@ -41,7 +41,7 @@ def normwise(a, b) -> float:
 
 
 def oracle_params(P, hp=3, beta0=0.5, eta=1.5, gamma=1.01, gamma_bar=1.005, project_w=0,
-                  compare_prev=0, lw=None, lh=None):
+                  compare_prev=1, lw=None, lh=None):
     if lw is None or lh is None:
         aw, ah = O.sweep_counts(P.m, P.n, P.nnz, P.r)
         lw = aw if lw is None else lw

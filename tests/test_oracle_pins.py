@@ -18,7 +18,9 @@ Which pin covers which oracle routine:
                                            ANLS monotone and exact per column;
                                            E-ANLS beats ANLS on low-rank data
   orc_beta_update                          hand-derived Algorithm 3 sequences
-  orc_eahals_*                             hand-worked 2x2 example, beta0 = 0
+  orc_eahals_*                             hand-worked 2x2 examples (accepted
+                                           steps; a restart; hp = 1; hp = 2),
+                                           beta0 = 0
                                            reduces to A-HALS, accepted errors
                                            monotone, hp=3 feasibility, exact
                                            power-of-two scaling equivariance,
@@ -286,6 +288,55 @@ def test_worked_example_2x2_rank1():
     assert st.s.beta_prev == pytest.approx(fin["beta_prev"], rel=1e-15)
 
 
+@pytest.mark.parametrize("name", ["worked_example_restart_2x2_r1", "worked_example_hp1_2x2_r1",
+                                  "worked_example_hp2_2x2_r1"])
+def test_worked_examples_step_by_step(name):
+    """Hand-worked 2x2 rank-1 runs in exact fractions (tests/golden/), checked
+    after every iteration: e(k), the beta it used, the decision, W, H, W_y,
+    H_y and the Algorithm 3 scalars.  The restart example pins steps 16-17
+    (W_y = W and H_y = H after the restart; beta/eta and beta_bar = beta_{k-1}
+    from Algorithm 3) and step 16 as written: its third iteration is accepted
+    because e(3) <= e(2), although e(3) exceeds the last accepted error e(1).
+    The hp = 2 example keeps a negative H_y (no projection); the hp = 1
+    example feeds H_n to the W-update and extrapolates H after it."""
+    with open(os.path.join(GOLDEN, name + ".json")) as f:
+        g = json.load(f)
+    pr = g["problem"]
+    X = np.array(pr["X"])
+    p = O.Params(hp=pr["hp"], beta0=pr["beta0"], eta=pr["eta"], gamma=pr["gamma"],
+                 gamma_bar=pr["gamma_bar"], lw=pr["lw"], lh=pr["lh"],
+                 compare_prev=pr["compare_prev"])
+    st = O.eahals_init(X, np.array(pr["W0"]), np.array(pr["H0"]), p)
+    assert st.s.e_last == pytest.approx(g["e0"], rel=1e-14)
+    for it in g["iterations"]:
+        e, b, acc = O.eahals_step(X, st, p)
+        num, den = (int(v) for v in it["e2_exact"].split("/"))
+        assert e * e == pytest.approx(num / den, rel=1e-12)
+        assert b == pytest.approx(it["beta_used"], rel=1e-15)
+        assert acc == bool(it["accepted"])
+        aft = it["after"]
+        for nm in ("W", "H", "Wy", "Hy"):
+            np.testing.assert_allclose(getattr(st, nm), np.array(aft[nm]), rtol=1e-12, atol=1e-14,
+                                       err_msg=f"{name} k={it['k']} {nm}")
+        assert st.s.beta == pytest.approx(aft["beta"], rel=1e-14)
+        assert st.s.beta_bar == pytest.approx(aft["beta_bar"], rel=1e-14)
+        assert st.s.beta_prev == pytest.approx(aft["beta_prev"], rel=1e-14)
+
+
+def test_restart_example_under_the_accepted_error_option():
+    """The option compare_prev = 0 (compare with the last accepted error)
+    restarts the restart example's third iteration, where step 16 as
+    written accepts: the two readings really differ on it."""
+    with open(os.path.join(GOLDEN, "worked_example_restart_2x2_r1.json")) as f:
+        g = json.load(f)
+    pr = g["problem"]
+    X = np.array(pr["X"])
+    p = O.Params(hp=3, beta0=pr["beta0"], lw=1, lh=1, compare_prev=0)
+    st = O.eahals_init(X, np.array(pr["W0"]), np.array(pr["H0"]), p)
+    _, _, ta = O.eahals_run(X, st, p, 3)
+    np.testing.assert_array_equal(ta, [True, False, False])
+
+
 @pytest.mark.parametrize("hp", [1, 2, 3])
 def test_beta0_zero_is_ahals(hp):
     P = wl.low_rank(40, 30, 5, seed=3, noise=0.05, dtype=np.float64)
@@ -299,7 +350,7 @@ def test_beta0_zero_is_ahals(hp):
     np.testing.assert_array_equal(te, tea)
 
 
-@pytest.mark.parametrize("hp,compare_prev", [(1, 0), (2, 0), (3, 0), (3, 1)])
+@pytest.mark.parametrize("hp,compare_prev", [(1, 1), (2, 1), (3, 1), (3, 0)])
 def test_restart_logic_and_accepted_errors(hp, compare_prev):
     P = wl.low_rank(60, 45, 6, seed=5, noise=0.02, dtype=np.float64)
     p = O.Params(hp=hp, beta0=0.75, eta=1.5, gamma=1.1, gamma_bar=1.05, lw=2, lh=3,

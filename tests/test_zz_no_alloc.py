@@ -67,3 +67,7 @@ def test_noalloc_rejects_oversized_input():
     st = lib.nmf_fro2_noalloc(X.data_ptr(), 1 << 15, 1 << 14, 1 << 14, out.data_ptr(), None)
     assert st == nmf.NMF_ENOTSUP
     assert "2^28" in nmf.nmf_last_error()
+    # m * n wraps to 1 in 64-bit arithmetic: still rejected, nothing launched
+    st = lib.nmf_fro2_noalloc(X.data_ptr(), 274177, 67280421310721, 67280421310721,
+                              out.data_ptr(), None)
+    assert st == nmf.NMF_ENOTSUP
