@@ -111,9 +111,14 @@ typedef struct {
 
 typedef struct {
     int64_t iters;           /* iterations run by this call                   */
-    double relerr;           /* e_last / ||X||_F at return                    */
+    double relerr;           /* ||X - W H||_F / ||X||_F of the returned pair
+                                (W, H) at return (nmf_eval_error)             */
+    double relerr_last;      /* e_last / ||X||_F at return: e(k) of the last
+                                accepted iteration, ||X - W_n H_y||_F, which
+                                for hp >= 2 is not the error of (W, H)        */
     double seconds;          /* wall time of the call                         */
     int32_t reached;         /* 1 when relerr <= target was observed          */
+    int32_t timed_out;       /* 1 when max_seconds ended the call early       */
 } nmf_result;
 
 typedef struct nmf_handle nmf_handle;
@@ -145,20 +150,50 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r,
                       void *stream);
 
 /* Enqueues `iters` outer iterations of Algorithm 2 (steps 3-20) with the
- * beta update of Algorithm 3 on the handle's stream; no host
- * synchronisation and no device-to-host traffic.  The restart decisions and
- * the beta schedule run on the device. */
-nmf_status nmf_step(nmf_handle *h, int32_t iters);
+ * beta update of Algorithm 3 on the handle's stream.  The restart decisions
+ * and the beta schedule run on the device.  With last == NULL there is no
+ * host synchronisation and no device-to-host traffic; otherwise the call
+ * synchronises the stream and fills *last as nmf_get_info does (e(k), the
+ * beta used and the decision of the last iteration among them).
+ * Errors: NMF_EINVAL for iters < 0; NMF_ECUDA from a launch. */
+nmf_status nmf_step(nmf_handle *h, int32_t iters, nmf_info *last);
 
-/* Runs up to max_iters iterations in chunks of `check_every` (>= 1),
- * reading e_last back after each chunk, and stops early once
- * e_last / ||X||_F <= target_relerr (target <= 0 disables the test).
- * Synchronises the stream; fills *res when res != NULL. */
+/* The error of the pair (W, H) the handle would return (the accepted
+ * iterate, Algorithm 2 step 19): err = ||X - W H||_F and relerr =
+ * err / ||X||_F, by Remark 1 (||X||^2 - 2<W, X H^T> + <W^T W, H H^T>, in
+ * the residual form of e(k)) from a fresh product X H^T (FP32 with
+ * compensated sums, in every precision mode) and H H^T accumulated
+ * error-free.  e(k) itself is ||X - W_n H_y||_F (step 15), which differs
+ * from this for hp >= 2.  Costs one pass over X; synchronises the stream.
+ * Either output may be NULL.  Errors: NMF_ENONFINITE, NMF_ECUDA. */
+nmf_status nmf_eval_error(nmf_handle *h, double *err, double *relerr);
+
+/* Runs Algorithm 2 for up to max_iters iterations in chunks of
+ * `check_every` (>= 1), the way the paper's experiments stop (Sec. 4: a
+ * target error or a fixed time budget).  After each chunk it synchronises
+ * and, when target_relerr > 0, evaluates the returned pair's relative
+ * error (nmf_eval_error, one pass over X per check) and stops once it is
+ * <= target_relerr; it also stops once max_seconds (> 0) of wall time have
+ * passed (0 = no limit).  Fills *res when res != NULL.
+ * Errors: NMF_EINVAL for max_iters < 0, check_every < 1, max_seconds < 0;
+ * a sticky device status (e.g. NMF_ENONFINITE) is returned as such. */
 nmf_status nmf_solve(nmf_handle *h, int64_t max_iters, double target_relerr,
-                     int32_t check_every, nmf_result *res);
+                     double max_seconds, int32_t check_every, nmf_result *res);
 
-/* Synchronises the stream and reports the scalar state. */
+/* Synchronises the stream and reports the scalar state of Algorithms 2
+ * and 3 (e(k), e_last, beta, beta_bar, beta_{k-1}, the last decision). */
 nmf_status nmf_get_info(nmf_handle *h, nmf_info *info);
+
+/* Decision replay: iteration k (0-based count of iterations done) takes
+ * the accept (1) / restart (0) decision accepted[k] instead of the test of
+ * step 16 of Algorithm 2, for k < count (count = 0 clears it).  Everything
+ * else -- e(k), both branches of Algorithm 3 -- runs unchanged, so a run
+ * can follow another implementation's sequence of decisions (where e(k)
+ * and e(k-1) are within round-off of each other, the two may take
+ * different branches and then different paths of the non-convex problem).
+ * A non-finite e(k) still restarts.  The array is copied; synchronises the
+ * stream.  Errors: NMF_EINVAL, NMF_ENOMEM, NMF_ECUDA. */
+nmf_status nmf_set_forced_decisions(nmf_handle *h, const uint8_t *accepted, int64_t count);
 
 /* Copies the accepted iterate (W, H) -- the pair Algorithm 2 returns --
  * into W (m x r) and H (r x n), host or device per to_device.  Either
@@ -194,8 +229,11 @@ nmf_status nmf_get_line_search_trace(nmf_handle *h, double *beta_star, int64_t c
                                      int64_t *len);
 
 /* Full solver state for checkpoint/resume and for replaying a step from an
- * identical state.  The four factor arrays are host or device per
- * on_device; sizes as above. */
+ * identical state: the pairs (W, H) and (W_y, H_y) of Algorithm 2 and the
+ * scalars of Algorithm 3 (beta, beta_bar, beta_{k-1}) with e_last / e(k-1).
+ * The four factor arrays are host or device per on_device; sizes as above.
+ * nmf_get_state synchronises; any array may be NULL to skip it.
+ * nmf_set_state needs all four; it resets the sticky device status. */
 typedef struct {
     double beta, beta_bar, beta_prev;  /* Algorithm 3 */
     double e_last;           /* error the next e(k) is compared with          */
@@ -240,6 +278,21 @@ nmf_status nmf_profile_phases(nmf_handle *h, int32_t iters, double *ms);
 nmf_status nmf_matmul_nt(const float *P, int64_t M, int64_t K, int64_t ldp, const float *Q,
                          int32_t q_rows, int64_t ldq, float *out, int64_t ldo,
                          int32_t precision, void *stream);
+
+/* Failure detection (the paper has no counterpart): every wait inside the
+ * tensor-core product kernel is bounded; when one runs out the kernel
+ * records it, drains its own copies and MMAs, frees its tensor memory and
+ * returns, and the call reports NMF_ETIMEOUT (nmf_matmul_nt) or the
+ * handle's device_status becomes NMF_ETIMEOUT.  This hook lets a test make
+ * one such wait run out on purpose without faulting anything: with
+ * extra > 0, the last CTA of a tile shared by several CTAs waits, in its
+ * final segment (no copy or MMA of it in flight), for `extra` partials that
+ * never arrive, so the bounded wait (about 0.1 s) expires.  extra = 0
+ * (the default) restores normal operation.  Applies to the current device;
+ * launches already enqueued are not affected predictably, so set it between
+ * synchronised calls.  A handle whose product timed out keeps stale tile
+ * counters: destroy it.  Errors: NMF_EINVAL for extra < 0, NMF_ECUDA. */
+nmf_status nmf_debug_set_fixup_stall(int32_t extra);
 
 /* Releases every device and host resource of the handle (NULL is a no-op).
  * Synchronises the stream first. */

@@ -54,7 +54,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
            _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -68,6 +68,8 @@ def _load():
     lib = ct.CDLL(build())
     vp = ct.c_void_p
     sig = {
+        "orc_set_threads": (None, [ct.c_int]),
+        "orc_get_threads": (ct.c_int, []),
         "orc_fro2": (ct.c_double, [vp]),
         "orc_wtx": (None, [vp, ct.c_int, _DP, _DP]),
         "orc_xht": (None, [vp, ct.c_int, _DP, _DP]),
@@ -181,6 +183,15 @@ class Scalars:
         self.beta, self.beta_bar, self.beta_prev = s.beta, s.beta_bar, s.beta_prev
         self.e_last, self.e_prev, self.k = s.e_last, s.e_prev, s.k
         return self
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (results do not depend on it)."""
+    _load().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 def fro2(X) -> float:

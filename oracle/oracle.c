@@ -8,12 +8,39 @@
  * Plain loops in double precision; the only freedom taken is the loop
  * nesting of sums whose order the paper does not fix.  Build with
  * -ffp-contract=off so that x86-64 and aarch64 give identical bits.
+ *
+ * Threads (OpenMP): only loops over independent outputs run in parallel --
+ * columns of A = W^T X, rows of C = X H^T, entries of a Gram, columns of H
+ * and rows of W in the sweeps and the exact NNLS, rows of the direct error
+ * -- and every output keeps the sequential summation order, so the result
+ * does not depend on the number of threads.
  */
 #include "oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 static double *orc_alloc(int64_t count)
 {
@@ -45,18 +72,25 @@ void orc_wtx(const orc_matrix *X, int r, const double *W, double *A)
 {
     const int64_t m = X->m, n = X->n;
     memset(A, 0, sizeof(double) * (size_t)r * (size_t)n);
-    for (int64_t i = 0; i < m; ++i) {
-        if (X->is_csr) {
+    if (X->is_csr) {
+        for (int64_t i = 0; i < m; ++i)
             for (int64_t p = X->rowptr[i]; p < X->rowptr[i + 1]; ++p) {
                 int64_t j = X->colidx[p];
                 for (int k = 0; k < r; ++k) A[k * n + j] += W[i * r + k] * X->val[p];
             }
-        } else {
+        return;
+    }
+    /* Dense: column blocks in parallel; each A(k,j) still sums over i in
+     * increasing order. */
+    const int64_t cb = 256;
+    #pragma omp parallel for schedule(dynamic)
+    for (int64_t j0 = 0; j0 < n; j0 += cb) {
+        const int64_t j1 = j0 + cb < n ? j0 + cb : n;
+        for (int64_t i = 0; i < m; ++i)
             for (int k = 0; k < r; ++k) {
                 double w = W[i * r + k];
-                for (int64_t j = 0; j < n; ++j) A[k * n + j] += w * X->x[i * n + j];
+                for (int64_t j = j0; j < j1; ++j) A[k * n + j] += w * X->x[i * n + j];
             }
-        }
     }
 }
 
@@ -64,6 +98,7 @@ void orc_wtx(const orc_matrix *X, int r, const double *W, double *A)
 void orc_xht(const orc_matrix *X, int r, const double *H, double *C)
 {
     const int64_t m = X->m, n = X->n;
+    #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < m; ++i) {
         for (int k = 0; k < r; ++k) {
             double s = 0.0;
@@ -81,6 +116,7 @@ void orc_xht(const orc_matrix *X, int r, const double *H, double *C)
 /* G(k,j) = W(:,k)^T W(:,j). */
 void orc_gram_w(int64_t m, int r, const double *W, double *G)
 {
+    #pragma omp parallel for schedule(dynamic)
     for (int k = 0; k < r; ++k)
         for (int j = 0; j < r; ++j) {
             double s = 0.0;
@@ -92,6 +128,7 @@ void orc_gram_w(int64_t m, int r, const double *W, double *G)
 /* D(k,j) = H(k,:) H(j,:)^T. */
 void orc_gram_h(int64_t n, int r, const double *H, double *D)
 {
+    #pragma omp parallel for schedule(dynamic)
     for (int k = 0; k < r; ++k)
         for (int j = 0; j < r; ++j) {
             double s = 0.0;
@@ -105,12 +142,12 @@ void orc_gram_h(int64_t n, int r, const double *H, double *D)
  *                    / ||W(:,k)||^2)
  * with A = W^T X and G = W^T W, so ||W(:,k)||^2 = G(k,k).  A zero
  * denominator (the paper does not treat it) leaves the row unchanged. */
-void orc_hals_row_h(int64_t n, int r, const double *A, const double *G,
-                    double *H, int k)
+static void hals_row_h_cols(int64_t n, int r, const double *A, const double *G,
+                            double *H, int k, int64_t c0, int64_t c1)
 {
     const double gkk = G[k * r + k];
     if (!(gkk > 0.0)) return;
-    for (int64_t c = 0; c < n; ++c) {
+    for (int64_t c = c0; c < c1; ++c) {
         double s = A[k * n + c];
         for (int j = 0; j < r; ++j) {
             if (j == k) continue;
@@ -121,17 +158,23 @@ void orc_hals_row_h(int64_t n, int r, const double *A, const double *G,
     }
 }
 
+void orc_hals_row_h(int64_t n, int r, const double *A, const double *G,
+                    double *H, int k)
+{
+    hals_row_h_cols(n, r, A, G, H, k, 0, n);
+}
+
 /* The same closed form for column k of W, from the symmetry
  * ||X - WH|| = ||X^T - H^T W^T|| (Sec. 1):
  *   W(:,k) = max(0, (X H(k,:)^T - sum_{j != k} W(:,j) (H(j,:) H(k,:)^T))
  *                    / ||H(k,:)||^2)
  * with C = X H^T and D = H H^T. */
-void orc_hals_col_w(int64_t m, int r, const double *C, const double *D,
-                    double *W, int k)
+static void hals_col_w_rows(int r, const double *C, const double *D, double *W, int k,
+                            int64_t i0, int64_t i1)
 {
     const double dkk = D[k * r + k];
     if (!(dkk > 0.0)) return;
-    for (int64_t i = 0; i < m; ++i) {
+    for (int64_t i = i0; i < i1; ++i) {
         double s = C[i * r + k];
         for (int j = 0; j < r; ++j) {
             if (j == k) continue;
@@ -142,20 +185,39 @@ void orc_hals_col_w(int64_t m, int r, const double *C, const double *D,
     }
 }
 
+void orc_hals_col_w(int64_t m, int r, const double *C, const double *D,
+                    double *W, int k)
+{
+    hals_col_w_rows(r, C, D, W, k, 0, m);
+}
+
 /* A-HALS: the rows of H are updated in cyclic order, and the whole pass is
- * repeated `sweeps` times reusing W^T W and W^T X (Sec. 1, second bullet). */
+ * repeated `sweeps` times reusing W^T W and W^T X (Sec. 1, second bullet).
+ * A column of H only ever reads itself, A and G, so blocks of columns run
+ * the whole sequence independently (in parallel); each column sees exactly
+ * the sequential order of updates. */
 void orc_hals_sweeps_h(int64_t n, int r, const double *A, const double *G,
                        double *H, int sweeps)
 {
-    for (int l = 0; l < sweeps; ++l)
-        for (int k = 0; k < r; ++k) orc_hals_row_h(n, r, A, G, H, k);
+    const int64_t cb = 64;
+    #pragma omp parallel for schedule(dynamic)
+    for (int64_t c0 = 0; c0 < n; c0 += cb) {
+        const int64_t c1 = c0 + cb < n ? c0 + cb : n;
+        for (int l = 0; l < sweeps; ++l)
+            for (int k = 0; k < r; ++k) hals_row_h_cols(n, r, A, G, H, k, c0, c1);
+    }
 }
 
 void orc_hals_sweeps_w(int64_t m, int r, const double *C, const double *D,
                        double *W, int sweeps)
 {
-    for (int l = 0; l < sweeps; ++l)
-        for (int k = 0; k < r; ++k) orc_hals_col_w(m, r, C, D, W, k);
+    const int64_t rb = 64;
+    #pragma omp parallel for schedule(dynamic)
+    for (int64_t i0 = 0; i0 < m; i0 += rb) {
+        const int64_t i1 = i0 + rb < m ? i0 + rb : m;
+        for (int l = 0; l < sweeps; ++l)
+            for (int k = 0; k < r; ++k) hals_col_w_rows(r, C, D, W, k, i0, i1);
+    }
 }
 
 /* Solves G_FF z = c for the free set F (Cholesky of the |F| x |F| block,
@@ -287,32 +349,43 @@ int orc_nnls(int r, const double *G, const double *b, double *x, int max_iter)
 /* Exact subproblems of ANLS: every column of H (G = W^T W, b = A[:, j])
  * and every row of W (G = D, b = C[i, :]), warm-started from the values
  * held in H and W.  Returns the largest exchange count, -1 on failure. */
+static int worse(int a, int b) { return (a < 0 || b < 0) ? -1 : (a > b ? a : b); }
+
 int orc_nnls_h(int64_t n, int r, const double *A, const double *G, double *H)
 {
-    double *b = orc_alloc(r), *x = orc_alloc(r);
     int worst = 0;
-    for (int64_t j = 0; j < n; ++j) {
-        for (int k = 0; k < r; ++k) {
-            b[k] = A[k * n + j];
-            x[k] = H[k * n + j];
+    #pragma omp parallel
+    {
+        double *b = orc_alloc(r), *x = orc_alloc(r);
+        int mine = 0;
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t j = 0; j < n; ++j) {
+            for (int k = 0; k < r; ++k) {
+                b[k] = A[k * n + j];
+                x[k] = H[k * n + j];
+            }
+            mine = worse(mine, orc_nnls(r, G, b, x, 100 * (r + 1)));
+            for (int k = 0; k < r; ++k) H[k * n + j] = x[k];
         }
-        const int st = orc_nnls(r, G, b, x, 100 * (r + 1));
-        if (st < 0) worst = -1;
-        else if (worst >= 0 && st > worst) worst = st;
-        for (int k = 0; k < r; ++k) H[k * n + j] = x[k];
+        #pragma omp critical
+        worst = worse(worst, mine);
+        free(b);
+        free(x);
     }
-    free(b);
-    free(x);
     return worst;
 }
 
 int orc_nnls_w(int64_t m, int r, const double *C, const double *D, double *W)
 {
     int worst = 0;
-    for (int64_t i = 0; i < m; ++i) {
-        const int st = orc_nnls(r, D, C + i * r, W + i * r, 100 * (r + 1));
-        if (st < 0) worst = -1;
-        else if (worst >= 0 && st > worst) worst = st;
+    #pragma omp parallel
+    {
+        int mine = 0;
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < m; ++i)
+            mine = worse(mine, orc_nnls(r, D, C + i * r, W + i * r, 100 * (r + 1)));
+        #pragma omp critical
+        worst = worse(worst, mine);
     }
     return worst;
 }
@@ -338,23 +411,32 @@ double orc_err2_direct(const orc_matrix *X, int r, const double *W,
                        const double *H)
 {
     const int64_t m = X->m, n = X->n;
-    double *row = orc_alloc(n);
-    double s = 0.0;
-    for (int64_t i = 0; i < m; ++i) {
-        for (int64_t j = 0; j < n; ++j) {
-            double wh = 0.0;
-            for (int k = 0; k < r; ++k) wh += W[i * r + k] * H[k * n + j];
-            row[j] = -wh;
+    double *rows = orc_alloc(m);     /* sum over row i, j ascending */
+    #pragma omp parallel
+    {
+        double *row = orc_alloc(n);
+        #pragma omp for schedule(dynamic, 8)
+        for (int64_t i = 0; i < m; ++i) {
+            for (int64_t j = 0; j < n; ++j) {
+                double wh = 0.0;
+                for (int k = 0; k < r; ++k) wh += W[i * r + k] * H[k * n + j];
+                row[j] = -wh;
+            }
+            if (X->is_csr) {
+                for (int64_t p = X->rowptr[i]; p < X->rowptr[i + 1]; ++p)
+                    row[X->colidx[p]] += X->val[p];
+            } else {
+                for (int64_t j = 0; j < n; ++j) row[j] += X->x[i * n + j];
+            }
+            double t = 0.0;
+            for (int64_t j = 0; j < n; ++j) t += row[j] * row[j];
+            rows[i] = t;
         }
-        if (X->is_csr) {
-            for (int64_t p = X->rowptr[i]; p < X->rowptr[i + 1]; ++p)
-                row[X->colidx[p]] += X->val[p];
-        } else {
-            for (int64_t j = 0; j < n; ++j) row[j] += X->x[i * n + j];
-        }
-        for (int64_t j = 0; j < n; ++j) s += row[j] * row[j];
+        free(row);
     }
-    free(row);
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) s += rows[i];
+    free(rows);
     return s;
 }
 
@@ -367,31 +449,45 @@ double orc_line_search_beta(const orc_matrix *X, int r, const double *W,
                             const double *Wn, const double *Hy)
 {
     const int64_t m = X->m, n = X->n;
-    double *res = orc_alloc(n), *dir = orc_alloc(n);
+    double *nums = orc_alloc(m), *dens = orc_alloc(m);   /* per row, j ascending */
+    #pragma omp parallel
+    {
+        double *res = orc_alloc(n), *dir = orc_alloc(n);
+        #pragma omp for schedule(dynamic, 8)
+        for (int64_t i = 0; i < m; ++i) {
+            for (int64_t j = 0; j < n; ++j) {
+                double wh = 0.0, dh = 0.0;
+                for (int k = 0; k < r; ++k) {
+                    wh += Wn[i * r + k] * Hy[k * n + j];
+                    dh += (Wn[i * r + k] - W[i * r + k]) * Hy[k * n + j];
+                }
+                res[j] = -wh;
+                dir[j] = dh;
+            }
+            if (X->is_csr) {
+                for (int64_t p = X->rowptr[i]; p < X->rowptr[i + 1]; ++p)
+                    res[X->colidx[p]] += X->val[p];
+            } else {
+                for (int64_t j = 0; j < n; ++j) res[j] += X->x[i * n + j];
+            }
+            double a = 0.0, b = 0.0;
+            for (int64_t j = 0; j < n; ++j) {
+                a += res[j] * dir[j];
+                b += dir[j] * dir[j];
+            }
+            nums[i] = a;
+            dens[i] = b;
+        }
+        free(res);
+        free(dir);
+    }
     double num = 0.0, den = 0.0;
     for (int64_t i = 0; i < m; ++i) {
-        for (int64_t j = 0; j < n; ++j) {
-            double wh = 0.0, dh = 0.0;
-            for (int k = 0; k < r; ++k) {
-                wh += Wn[i * r + k] * Hy[k * n + j];
-                dh += (Wn[i * r + k] - W[i * r + k]) * Hy[k * n + j];
-            }
-            res[j] = -wh;
-            dir[j] = dh;
-        }
-        if (X->is_csr) {
-            for (int64_t p = X->rowptr[i]; p < X->rowptr[i + 1]; ++p)
-                res[X->colidx[p]] += X->val[p];
-        } else {
-            for (int64_t j = 0; j < n; ++j) res[j] += X->x[i * n + j];
-        }
-        for (int64_t j = 0; j < n; ++j) {
-            num += res[j] * dir[j];
-            den += dir[j] * dir[j];
-        }
+        num += nums[i];
+        den += dens[i];
     }
-    free(res);
-    free(dir);
+    free(nums);
+    free(dens);
     return den > 0.0 ? num / den : 0.0;
 }
 

@@ -65,6 +65,11 @@ typedef struct {
     int64_t k;                /* iterations done                         */
 } orc_scalars;
 
+/* Threads used by the parallel loops (OpenMP; results do not depend on
+ * it).  orc_set_threads(n <= 0) leaves the setting unchanged. */
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
 /* ||X||_F^2 (Remark 1). */
 double orc_fro2(const orc_matrix *X);
 

@@ -110,6 +110,9 @@ struct nmf_handle {
     double *tr_bstar = nullptr;                  // line-search diagnostic (optional)
     unsigned char *tr_acc = nullptr;
     int64_t tr_cap = 0;
+    unsigned char *forced = nullptr;             // decision replay (nmf_set_forced_decisions)
+    int64_t forced_len = 0;
+    double *eval = nullptr;                      // nmf_eval_error: e^2, e of (W, H)
     int64_t k_enq = 0;                           // iterations enqueued so far
     // graph of one iteration
     cudaGraphExec_t exec = nullptr;
@@ -132,7 +135,7 @@ void free_handle(nmf_handle *h) {
                     h->C_lo, h->D_lo, h->Wt, h->Wq, h->Hq, h->Pc, h->Pc_lo, h->Pa, h->Pa_lo, h->Wth,
                     h->Wtl, h->Hh, h->Hl, h->tct_c, h->tct_a, h->tc_err,
                     h->fro2, h->state, h->partials, h->counter, h->tickets, h->xtickets, h->ws, h->flag,
-                    h->tr_e, h->tr_beta, h->tr_acc, h->tr_bstar};
+                    h->tr_e, h->tr_beta, h->tr_acc, h->tr_bstar, h->forced, h->eval};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->h_state) cudaFreeHost(h->h_state);
@@ -308,6 +311,8 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
     wep.trace.acc = h->tr_acc;
     wep.trace.cap = h->tr_cap;
     wep.trace.bstar = h->tr_bstar;
+    wep.trace.forced = h->forced;
+    wep.trace.forced_len = h->forced_len;
     wep.W_prev = h->p.line_search_trace ? h->W : nullptr;
     NMF_STEP(launch_hals_w(h->m, h->r, h->rs, h->C, h->D, h->Wy, h->Wn, h->lw, wep, st));
     NMF_STEP(mark(NMF_PHASE_FINALIZE));
@@ -569,6 +574,7 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     NMF_TRYC(dalloc(&h->D, rs * rs));
     NMF_TRYC(dalloc(&h->D_lo, rs * rs));
     NMF_TRYC(dalloc(&h->fro2, 1));
+    NMF_TRYC(dalloc(&h->eval, 2));
     NMF_TRYC(dalloc(&h->state, 1));
     NMF_TRYC(dalloc(&h->flag, 1));
     const int npart = std::max(hals_w_num_ctas(m, r), err_rows_num_ctas(m));
@@ -724,13 +730,14 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     return NMF_OK;
 }
 
-nmf_status nmf_step(nmf_handle *h, int32_t iters) {
+nmf_status nmf_step(nmf_handle *h, int32_t iters, nmf_info *last) {
     if (!h) return fail(NMF_EINVAL, "handle is NULL");
     if (iters < 0) return fail(NMF_EINVAL, "iters must be >= 0");
     nmf_status s = ensure_trace(h, h->k_enq + iters);
     if (s != NMF_OK) return s;
     for (int32_t i = 0; i < iters; ++i) NMF_CUDA(cudaGraphLaunch(h->exec, h->st));
     h->k_enq += iters;
+    if (last) return nmf_get_info(h, last);
     return NMF_OK;
 }
 
@@ -765,40 +772,101 @@ nmf_status nmf_get_info(nmf_handle *h, nmf_info *info) {
     return NMF_OK;
 }
 
-nmf_status nmf_solve(nmf_handle *h, int64_t max_iters, double target_relerr, int32_t check_every,
-                     nmf_result *res) {
+nmf_status nmf_eval_error(nmf_handle *h, double *err, double *relerr) {
     if (!h) return fail(NMF_EINVAL, "handle is NULL");
-    if (max_iters < 0 || check_every < 1) return fail(NMF_EINVAL, "bad max_iters / check_every");
+    cudaStream_t st = h->st;
+    // C, C_lo, D and D_lo are rebuilt by every iteration before they are
+    // read, so they serve as scratch here.  FP32 compensated products in
+    // every precision mode: the yardstick is the same for all of them.
+    NMF_CUDA(launch_gram_cols(h->H, h->n, h->ld, h->r, h->rs, h->D, h->D_lo, h->ws, st));
+    if (h->is_csr) {
+        NMF_CUDA(enqueue_xht(h, h->H, st));
+    } else {
+        NMF_CUDA(launch_xht_f32(h->X, h->m, h->ld, h->r, h->H, h->ld, h->C, h->C_lo, h->rs,
+                                h->ws, h->xtickets, st));
+    }
+    NMF_CUDA(launch_err_rows(h->m, h->r, h->rs, h->W, h->C, h->C_lo, h->D, h->D_lo, h->partials,
+                             st));
+    NMF_CUDA(launch_pair_error(h->m, h->fro2, h->partials, h->eval, st));
+    double out[2] = {0.0, 0.0}, f2 = 0.0;
+    NMF_CUDA(cudaMemcpyAsync(out, h->eval, sizeof(out), cudaMemcpyDeviceToHost, st));
+    NMF_CUDA(cudaMemcpyAsync(&f2, h->fro2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NMF_CUDA(cudaStreamSynchronize(st));
+    if (!std::isfinite(out[0])) return fail(NMF_ENONFINITE, "the error of (W, H) is not finite");
+    if (err) *err = out[1];
+    if (relerr) *relerr = f2 > 0.0 ? out[1] / sqrt(f2) : 0.0;
+    return NMF_OK;
+}
+
+nmf_status nmf_solve(nmf_handle *h, int64_t max_iters, double target_relerr, double max_seconds,
+                     int32_t check_every, nmf_result *res) {
+    if (!h) return fail(NMF_EINVAL, "handle is NULL");
+    if (max_iters < 0 || check_every < 1 || !(max_seconds >= 0.0))
+        return fail(NMF_EINVAL, "bad max_iters / check_every / max_seconds");
     auto t0 = std::chrono::steady_clock::now();
+    auto elapsed = [&]() {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
     int64_t done = 0;
-    int reached = 0;
+    int reached = 0, timed_out = 0;
+    double rel = -1.0;
     nmf_info info{};
+    nmf_status s;
     while (done < max_iters) {
         const int32_t chunk = (int32_t)std::min<int64_t>(check_every, max_iters - done);
-        nmf_status s = nmf_step(h, chunk);
+        s = nmf_step(h, chunk, &info);
         if (s != NMF_OK) return s;
         done += chunk;
-        s = nmf_get_info(h, &info);
-        if (s != NMF_OK) return s;
         if (info.device_status != 0)
             return fail((nmf_status)info.device_status, "device reported status %d after %lld iterations",
                         info.device_status, (long long)info.k);
-        if (target_relerr > 0.0 && info.relerr <= target_relerr) {
-            reached = 1;
+        if (target_relerr > 0.0) {
+            s = nmf_eval_error(h, nullptr, &rel);
+            if (s != NMF_OK) return s;
+            if (rel <= target_relerr) {
+                reached = 1;
+                break;
+            }
+        }
+        if (max_seconds > 0.0 && elapsed() >= max_seconds) {
+            timed_out = done < max_iters;
             break;
         }
     }
-    if (done == 0) {
-        nmf_status s = nmf_get_info(h, &info);
+    if (rel < 0.0) {
+        s = nmf_eval_error(h, nullptr, &rel);
         if (s != NMF_OK) return s;
     }
+    s = nmf_get_info(h, &info);
+    if (s != NMF_OK) return s;
     if (res) {
         res->iters = done;
-        res->relerr = info.relerr;
-        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        res->relerr = rel;
+        res->relerr_last = info.relerr;
+        res->seconds = elapsed();
         res->reached = reached;
+        res->timed_out = timed_out;
     }
     return NMF_OK;
+}
+
+nmf_status nmf_set_forced_decisions(nmf_handle *h, const uint8_t *accepted, int64_t count) {
+    if (!h || count < 0 || (count > 0 && !accepted))
+        return fail(NMF_EINVAL, "nmf_set_forced_decisions: bad arguments");
+    NMF_CUDA(cudaStreamSynchronize(h->st));
+    unsigned char *d = nullptr;
+    if (count > 0) {
+        NMF_CUDA(cudaMalloc(&d, (size_t)count));
+        cudaError_t e = cudaMemcpy(d, accepted, (size_t)count, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return fail(NMF_ECUDA, "nmf_set_forced_decisions: %s", cudaGetErrorString(e));
+        }
+    }
+    if (h->forced) cudaFree(h->forced);
+    h->forced = d;
+    h->forced_len = count;
+    return build_graph(h);        // the decision kernel takes the array by value
 }
 
 static nmf_status copy_w_out(nmf_handle *h, const float *src, float *dst, int to_device) {
@@ -1016,6 +1084,12 @@ nmf_status nmf_matmul_nt(const float *P, int64_t M, int64_t K, int64_t ldp, cons
         return fail(e == cudaErrorMemoryAllocation ? NMF_ENOMEM : NMF_ECUDA, "nmf_matmul_nt: %s",
                     cudaGetErrorString(e));
     if (flag) return fail(NMF_ETIMEOUT, "nmf_matmul_nt: a bounded tensor-core pipeline wait expired");
+    return NMF_OK;
+}
+
+nmf_status nmf_debug_set_fixup_stall(int32_t extra) {
+    if (extra < 0) return fail(NMF_EINVAL, "nmf_debug_set_fixup_stall: extra must be >= 0");
+    NMF_CUDA(tc_set_fixup_stall(extra));
     return NMF_OK;
 }
 

@@ -45,6 +45,8 @@ struct DevTrace {
     unsigned char *acc;
     double *bstar;        // line-search step of Sec. 3 per iteration, or null
     long long cap;
+    const unsigned char *forced;  // decision replay: iteration k takes forced[k]
+    long long forced_len;         // (for k < forced_len) instead of the test
 };
 
 // Error reduction partials of one W-sweep launch (Remark 1 in residual
@@ -139,6 +141,10 @@ cudaError_t launch_err_rows(int64_t m, int r, int rs, const float *W, const floa
                             const float *C_lo, const float *D, const float *D_lo,
                             ErrPartial *part, cudaStream_t st);
 
+// e^2 and e of a pair from the launch_err_rows partials (out[0], out[1]).
+cudaError_t launch_pair_error(int64_t m, const double *fro2, const ErrPartial *partials,
+                              double *out, cudaStream_t st);
+
 // e(0) (Algorithm 2 step 1) and the initial Algorithm 3 values.
 cudaError_t launch_init_state(int64_t m, int r, int rs, const float *W, const float *C,
                               const float *C_lo, const float *D, const float *D_lo,
@@ -176,6 +182,9 @@ cudaError_t launch_tc_pack(const float *x, int64_t rows, int64_t cols, int64_t l
 size_t tc_ws_bytes(int64_t M, int64_t K, int N, int precision);
 int64_t tc_num_tickets(int64_t M);
 bool tc_available();
+// Failure-detection hook: the last CTA of a shared tile waits, in its final
+// segment, for `extra` partials that never come (see tc_products.cu).
+cudaError_t tc_set_fixup_stall(int extra);
 cudaError_t launch_tc_product(const TcOperands &o, int precision, bool transposed_out, float *out,
                               int64_t out_ld, void *ws, unsigned int *tickets, int *err_flag,
                               cudaStream_t st);

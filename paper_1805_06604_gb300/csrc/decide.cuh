@@ -1,0 +1,51 @@
+// decide.cuh -- the restart decision of Algorithm 2 (steps 16-20) and the
+// beta schedule of Algorithm 3 (Ang & Gillis, arXiv 1805.06604), taken on
+// the device by one thread of the W-sweep kernel's last CTA once e(k) is
+// known (Remark 1), so no iteration reads anything back to the host.
+#pragma once
+#include <math.h>
+
+#include "common.cuh"
+
+namespace nmfg {
+
+// Algorithm 3 and steps 16-20 of Algorithm 2, run by one thread.
+__device__ __forceinline__ void decide_and_update_beta(DevState *s, const DevParams &p, const DevTrace &t,
+                                       double cross, double quad, double bnum, double bden) {
+    // Remark 1 in residual form: ||X||^2 - <W_n, C> + <W_n, W_n D - C>.
+    const double e2 = s->fro2 - cross + quad;
+    const double e = sqrt(e2 > 0.0 ? e2 : 0.0);
+    const int finite = isfinite(e2) ? 1 : 0;
+    if (!finite) s->status = (int)NMF_ENONFINITE;
+    const double ref = p.compare_prev ? s->e_prev : s->e_last;
+    const long long k = s->k;
+    int acc = finite && !(e > ref);                                   // restart only if e(k) > ref
+    if (t.forced != nullptr && k < t.forced_len) acc = finite && t.forced[k] != 0;
+    if (k < t.cap) {
+        t.e[k] = e;
+        t.beta[k] = s->beta;
+        t.acc[k] = (unsigned char)acc;
+        // Sec. 3's line-search step for this W-update (diagnostic only).
+        if (t.bstar) t.bstar[k] = bden > 0.0 ? bnum / bden : 0.0;
+    }
+    s->beta_used = s->beta;
+    s->e_k = e;
+    s->accepted = acc;
+    if (acc) s->e_last = e;
+    s->e_prev = e;
+    double next;
+    if (acc) {
+        const double grown = p.gamma * s->beta;
+        next = grown < s->beta_bar ? grown : s->beta_bar;
+        const double bar = p.gamma_bar * s->beta_bar;
+        s->beta_bar = bar < 1.0 ? bar : 1.0;
+    } else {
+        next = s->beta / p.eta;
+        s->beta_bar = s->beta_prev;
+    }
+    s->beta_prev = s->beta;
+    s->beta = next;
+    s->k = k + 1;
+}
+
+}  // namespace nmfg

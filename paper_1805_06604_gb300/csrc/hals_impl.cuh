@@ -36,6 +36,7 @@
 #include <utility>
 
 #include "common.cuh"
+#include "decide.cuh"
 
 namespace nmfg {
 namespace {
@@ -65,44 +66,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
-}
-
-// Algorithm 3 and steps 16-20 of Algorithm 2, run by one thread.
-__device__ void decide_and_update_beta(DevState *s, const DevParams &p, const DevTrace &t,
-                                       double cross, double quad, double bnum, double bden) {
-    // Remark 1 in residual form: ||X||^2 - <W_n, C> + <W_n, W_n D - C>.
-    const double e2 = s->fro2 - cross + quad;
-    const double e = sqrt(e2 > 0.0 ? e2 : 0.0);
-    const int finite = isfinite(e2) ? 1 : 0;
-    if (!finite) s->status = (int)NMF_ENONFINITE;
-    const double ref = p.compare_prev ? s->e_prev : s->e_last;
-    const int acc = finite && !(e > ref);                             // restart only if e(k) > ref
-    const long long k = s->k;
-    if (k < t.cap) {
-        t.e[k] = e;
-        t.beta[k] = s->beta;
-        t.acc[k] = (unsigned char)acc;
-        // Sec. 3's line-search step for this W-update (diagnostic only).
-        if (t.bstar) t.bstar[k] = bden > 0.0 ? bnum / bden : 0.0;
-    }
-    s->beta_used = s->beta;
-    s->e_k = e;
-    s->accepted = acc;
-    if (acc) s->e_last = e;
-    s->e_prev = e;
-    double next;
-    if (acc) {
-        const double grown = p.gamma * s->beta;
-        next = grown < s->beta_bar ? grown : s->beta_bar;
-        const double bar = p.gamma_bar * s->beta_bar;
-        s->beta_bar = bar < 1.0 ? bar : 1.0;
-    } else {
-        next = s->beta / p.eta;
-        s->beta_bar = s->beta_prev;
-    }
-    s->beta_prev = s->beta;
-    s->beta = next;
-    s->k = k + 1;
 }
 
 // Per-lane share of P_kk: the owner adds a_kk; every lane subtracts
@@ -534,4 +497,5 @@ cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const 
         int64_t, int, int64_t, const float *, const float *, int, const float *, float *, int,  \
         const nmfg::HEpilogue &, const nmfg::WEpilogue &, int, cudaStream_t);
 // Both sides.
-#define NMF_HALS_INSTANTIATE(TV, SV) NMF_HALS_INSTANTIATE_ONE(TV, SV, 0) NMF_HALS_INSTANTIATE_ONE(TV, SV, 1)
+// The W side (rows of W, item layout kRow).
+#define NMF_HALS_INSTANTIATE_ROWS(TV, SV) NMF_HALS_INSTANTIATE_ONE(TV, SV, 1)

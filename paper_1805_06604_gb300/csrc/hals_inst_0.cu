@@ -2,7 +2,7 @@
 // (hals_impl.cuh) for (lanes, slots) = (4, 32), (2, 28), (2, 19), (2, 9).
 #include "hals_impl.cuh"
 
-NMF_HALS_INSTANTIATE(4, 32)
-NMF_HALS_INSTANTIATE(2, 28)
-NMF_HALS_INSTANTIATE(2, 19)
-NMF_HALS_INSTANTIATE(2, 9)
+NMF_HALS_INSTANTIATE_ROWS(4, 32)
+NMF_HALS_INSTANTIATE_ROWS(2, 28)
+NMF_HALS_INSTANTIATE_ROWS(2, 19)
+NMF_HALS_INSTANTIATE_ROWS(2, 9)

@@ -2,8 +2,8 @@
 // (hals_impl.cuh) for (lanes, slots) = (4, 30), (2, 29), (2, 21), (2, 11), (2, 4).
 #include "hals_impl.cuh"
 
-NMF_HALS_INSTANTIATE(4, 30)
-NMF_HALS_INSTANTIATE(2, 29)
-NMF_HALS_INSTANTIATE(2, 21)
-NMF_HALS_INSTANTIATE(2, 11)
-NMF_HALS_INSTANTIATE(2, 4)
+NMF_HALS_INSTANTIATE_ROWS(4, 30)
+NMF_HALS_INSTANTIATE_ROWS(2, 29)
+NMF_HALS_INSTANTIATE_ROWS(2, 21)
+NMF_HALS_INSTANTIATE_ROWS(2, 11)
+NMF_HALS_INSTANTIATE_ROWS(2, 4)

@@ -2,8 +2,8 @@
 // (hals_impl.cuh) for (lanes, slots) = (4, 26), (4, 20), (2, 25), (2, 15), (2, 7).
 #include "hals_impl.cuh"
 
-NMF_HALS_INSTANTIATE(4, 26)
-NMF_HALS_INSTANTIATE(4, 20)
-NMF_HALS_INSTANTIATE(2, 25)
-NMF_HALS_INSTANTIATE(2, 15)
-NMF_HALS_INSTANTIATE(2, 7)
+NMF_HALS_INSTANTIATE_ROWS(4, 26)
+NMF_HALS_INSTANTIATE_ROWS(4, 20)
+NMF_HALS_INSTANTIATE_ROWS(2, 25)
+NMF_HALS_INSTANTIATE_ROWS(2, 15)
+NMF_HALS_INSTANTIATE_ROWS(2, 7)

@@ -2,8 +2,8 @@
 // (hals_impl.cuh) for (lanes, slots) = (4, 25), (2, 32), (2, 26), (2, 16), (2, 2).
 #include "hals_impl.cuh"
 
-NMF_HALS_INSTANTIATE(4, 25)
-NMF_HALS_INSTANTIATE(2, 32)
-NMF_HALS_INSTANTIATE(2, 26)
-NMF_HALS_INSTANTIATE(2, 16)
-NMF_HALS_INSTANTIATE(2, 2)
+NMF_HALS_INSTANTIATE_ROWS(4, 25)
+NMF_HALS_INSTANTIATE_ROWS(2, 32)
+NMF_HALS_INSTANTIATE_ROWS(2, 26)
+NMF_HALS_INSTANTIATE_ROWS(2, 16)
+NMF_HALS_INSTANTIATE_ROWS(2, 2)

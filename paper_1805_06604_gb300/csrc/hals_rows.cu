@@ -1,5 +1,7 @@
-// hals.cu -- dispatch of the A-HALS sweep kernel (hals_impl.cuh): picks the
-// lanes per item T and the smallest instantiated slot count S >= ceil(r/T).
+// hals_rows.cu -- dispatch of the lane-pipelined A-HALS sweep kernel
+// (hals_impl.cuh) on the rows of W: picks the lanes per item T and the
+// smallest instantiated slot count S >= ceil(r/T).  (The H side runs the
+// blocked kernel of sweeps.cu.)
 #include "common.cuh"
 
 namespace nmfg {
@@ -84,13 +86,6 @@ int hals_w_num_ctas(int64_t m, int r) {
     const int T = pick_lanes(r);
     const int64_t per_cta = cta_threads(m, T) / T;
     return (int)((m + per_cta - 1) / per_cta);
-}
-
-cudaError_t launch_hals_h(int64_t n, int64_t ldh, int r, int rs, const float *A,
-                          const float *G, const float *H_in, float *H_out, int sweeps,
-                          const HEpilogue &ep, cudaStream_t st) {
-    WEpilogue none{};
-    return dispatch<0>(n, r, ldh, A, G, rs, H_in, H_out, sweeps, ep, none, st);
 }
 
 cudaError_t launch_hals_w(int64_t m, int r, int rs, const float *C, const float *D,

@@ -341,6 +341,21 @@ err_rows_kernel(int64_t m, int r, int rs, const float *__restrict__ W,
     }
 }
 
+// Remark 1 (residual form) of a given pair from the err_rows partials:
+// out[0] = e^2 = ||X||^2 - cross + quad (unclamped), out[1] = sqrt(max(0, e^2)).
+__global__ void pair_error_kernel(const ErrPartial *__restrict__ part, int nparts,
+                                  const double *__restrict__ fro2, double *__restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double c = 0.0, q = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+        c += part[p].cross;
+        q += part[p].quad;
+    }
+    const double e2 = *fro2 - c + q;
+    out[0] = e2;
+    out[1] = sqrt(e2 > 0.0 ? e2 : 0.0);
+}
+
 __global__ void init_state_kernel(const ErrPartial *__restrict__ part, int nparts,
                                   const double *__restrict__ fro2, DevState *__restrict__ s,
                                   double beta0) {
@@ -468,6 +483,12 @@ cudaError_t launch_init_state(int64_t m, int r, int rs, const float *W, const fl
     cudaError_t e = launch_err_rows(m, r, rs, W, C, C_lo, D, D_lo, partials, st);
     if (e != cudaSuccess) return e;
     init_state_kernel<<<1, 32, 0, st>>>(partials, err_rows_num_ctas(m), fro2, state, beta0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_error(int64_t m, const double *fro2, const ErrPartial *partials,
+                              double *out, cudaStream_t st) {
+    pair_error_kernel<<<1, 32, 0, st>>>(partials, err_rows_num_ctas(m), fro2, out);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,12 @@ constexpr int kBM = 128;
 constexpr int kAtom = 128;                      // bytes per swizzled row
 constexpr unsigned long long kSpinLimit = 1ull << 26;
 
+// Failure-detection hook (nmf_debug_set_fixup_stall): extra partials the
+// last CTA of a shared tile waits for in its final segment -- when none of
+// its copies or MMAs is in flight -- so a test can make that bounded wait
+// run out without faulting anything.  0 in normal use.
+__device__ int g_fixup_stall = 0;
+
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -597,7 +603,8 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
             // Last CTA: the others have arrived, so they are running and
             // their partials land shortly (bounded wait on the count).
             if (threadIdx.x == 0) {
-                const unsigned int want = (unsigned)(last - first);
+                const unsigned int want =
+                    (unsigned)(last - first) + (seg == segs.n - 1 ? (unsigned)g_fixup_stall : 0u);
                 int ok = 0;
                 for (int i = 0; i < (1 << 20); ++i) {          // ~1 s at most
                     if (atomicAdd(written, 0u) >= want) {
@@ -1055,6 +1062,10 @@ cudaError_t launch_tc_pack(const float *x, int64_t rows, int64_t cols, int64_t l
 }
 
 bool tc_available() { return encode_fn() != nullptr; }
+
+cudaError_t tc_set_fixup_stall(int extra) {
+    return cudaMemcpyToSymbol(g_fixup_stall, &extra, sizeof(int));
+}
 
 cudaError_t launch_tc_product(const TcOperands &o, int precision, bool transposed_out, float *out,
                               int64_t out_ld, void *ws, unsigned int *tickets, int *err_flag,

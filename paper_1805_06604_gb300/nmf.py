@@ -52,8 +52,8 @@ class nmf_info(ct.Structure):
 
 
 class nmf_result(ct.Structure):
-    _fields_ = [("iters", ct.c_int64), ("relerr", ct.c_double), ("seconds", ct.c_double),
-                ("reached", ct.c_int32)]
+    _fields_ = [("iters", ct.c_int64), ("relerr", ct.c_double), ("relerr_last", ct.c_double),
+                ("seconds", ct.c_double), ("reached", ct.c_int32), ("timed_out", ct.c_int32)]
 
 
 class nmf_scalars(ct.Structure):
@@ -68,8 +68,11 @@ _SIGS = {
                          ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)],
     "nmf_create": [ct.POINTER(ct.c_void_p), ct.POINTER(nmf_matrix), ct.c_int32, ct.c_void_p,
                    ct.c_void_p, ct.c_int32, ct.POINTER(nmf_params), ct.c_void_p],
-    "nmf_step": [ct.c_void_p, ct.c_int32],
-    "nmf_solve": [ct.c_void_p, ct.c_int64, ct.c_double, ct.c_int32, ct.POINTER(nmf_result)],
+    "nmf_step": [ct.c_void_p, ct.c_int32, ct.c_void_p],
+    "nmf_solve": [ct.c_void_p, ct.c_int64, ct.c_double, ct.c_double, ct.c_int32,
+                  ct.POINTER(nmf_result)],
+    "nmf_eval_error": [ct.c_void_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)],
+    "nmf_set_forced_decisions": [ct.c_void_p, ct.c_void_p, ct.c_int64],
     "nmf_get_info": [ct.c_void_p, ct.POINTER(nmf_info)],
     "nmf_get_factors": [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int32],
     "nmf_get_extrapolated": [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int32],
@@ -85,6 +88,7 @@ _SIGS = {
     "nmf_fro2_noalloc": [ct.c_void_p, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_void_p,
                          ct.c_void_p],
     "nmf_destroy": [ct.c_void_p],
+    "nmf_debug_set_fixup_stall": [ct.c_int32],
     "nmf_batch_create": [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_void_p, ct.c_void_p,
                          ct.c_void_p, ct.c_void_p, ct.c_int32, ct.POINTER(nmf_params),
                          ct.c_void_p],
@@ -232,15 +236,35 @@ def nmf_create(X=None, r: int = 1, W0=None, H0=None, params: nmf_params | None =
     return h
 
 
-def nmf_step(h, iters: int = 1):
-    _check(load().nmf_step(h, int(iters)), "nmf_step")
+def nmf_step(h, iters: int = 1, last: bool = False):
+    """Enqueues `iters` iterations; with last=True also synchronises and
+    returns the nmf_info of the last one."""
+    info = nmf_info() if last else None
+    _check(load().nmf_step(h, int(iters), ct.byref(info) if last else None), "nmf_step")
+    return info
 
 
-def nmf_solve(h, max_iters: int, target_relerr: float = 0.0, check_every: int = 10) -> nmf_result:
+def nmf_solve(h, max_iters: int, target_relerr: float = 0.0, max_seconds: float = 0.0,
+              check_every: int = 10) -> nmf_result:
     res = nmf_result()
-    _check(load().nmf_solve(h, int(max_iters), float(target_relerr), int(check_every),
-                            ct.byref(res)), "nmf_solve")
+    _check(load().nmf_solve(h, int(max_iters), float(target_relerr), float(max_seconds),
+                            int(check_every), ct.byref(res)), "nmf_solve")
     return res
+
+
+def nmf_eval_error(h):
+    """(||X - WH||_F, relative error) of the pair (W, H) the handle returns."""
+    e, rel = ct.c_double(), ct.c_double()
+    _check(load().nmf_eval_error(h, ct.byref(e), ct.byref(rel)), "nmf_eval_error")
+    return e.value, rel.value
+
+
+def nmf_set_forced_decisions(h, accepted):
+    """Decision replay: iteration k takes accepted[k] (bool) instead of the
+    restart test; an empty sequence clears it."""
+    a = np.ascontiguousarray(np.asarray(accepted, dtype=np.uint8))
+    _check(load().nmf_set_forced_decisions(h, a.ctypes.data if a.size else None, int(a.size)),
+           "nmf_set_forced_decisions")
 
 
 def nmf_get_info(h) -> nmf_info:
@@ -327,6 +351,12 @@ def nmf_fro2_noalloc(X, out, stream=None):
         raise TypeError("out must hold at least one float64")
     _check(load().nmf_fro2_noalloc(X.data_ptr(), X.shape[0], X.shape[1], X.stride(0),
                                    out.data_ptr(), _stream_ptr(stream)), "nmf_fro2_noalloc")
+
+
+def nmf_debug_set_fixup_stall(extra: int):
+    """Failure-detection hook: make the tensor-core product's bounded fix-up
+    wait run out (extra > 0) or restore normal operation (0)."""
+    _check(load().nmf_debug_set_fixup_stall(int(extra)), "nmf_debug_set_fixup_stall")
 
 
 def nmf_destroy(h):
@@ -428,11 +458,17 @@ class Solver:
         self.r = int(r)
         self.h = nmf_create(X, r, W0, H0, self.params, stream, csr=csr, m=m, n=n)
 
-    def step(self, iters: int = 1):
-        nmf_step(self.h, iters)
+    def step(self, iters: int = 1, last: bool = False):
+        return nmf_step(self.h, iters, last)
 
-    def solve(self, max_iters, target_relerr=0.0, check_every=10):
-        return nmf_solve(self.h, max_iters, target_relerr, check_every)
+    def solve(self, max_iters, target_relerr=0.0, max_seconds=0.0, check_every=10):
+        return nmf_solve(self.h, max_iters, target_relerr, max_seconds, check_every)
+
+    def eval_error(self):
+        return nmf_eval_error(self.h)
+
+    def force_decisions(self, accepted):
+        nmf_set_forced_decisions(self.h, accepted)
 
     def info(self) -> nmf_info:
         return nmf_get_info(self.h)

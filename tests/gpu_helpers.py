@@ -24,7 +24,15 @@ def step_tol(kappa: float) -> float:
 
 
 def gram_kappa(st) -> float:
+    """Condition number of the Grams the two NNLS subproblems see.  A
+    coordinate whose Gram diagonal is zero (a zero column of W_y or row of
+    H_y) is skipped by the HALS update and takes no part in the subproblem,
+    so the condition number is that of the Gram restricted to the others."""
     def cond(M):
+        keep = np.diag(M) > 0.0
+        M = M[np.ix_(keep, keep)]
+        if M.size == 0:
+            return 1.0
         ev = np.linalg.eigvalsh(M)
         return float(ev[-1] / max(ev[0], ev[-1] * 1e-16))
     return max(cond(st.Wy.T @ st.Wy), cond(st.Hy @ st.Hy.T))
@@ -103,3 +111,31 @@ def single_step(P, p: O.Params, warm: int):
                 orc=dict(W=st.W, H=st.H, Wy=st.Wy, Hy=st.Hy, e=e_o, beta=b_o, acc=acc_o,
                          scalars=st.s),
                 fro2=O.fro2(Xo), kappa=kappa, tol=step_tol(kappa))
+
+
+def direct_relerr_gpu(P, W, H) -> float:
+    """||X - W H||_F / ||X||_F of host factors, evaluated in FP64 with torch
+    on the GPU (row blocks for dense X; for CSR X as ||X||^2 - 2<X, WH> +
+    <W^T W, H H^T>, <X, WH> entry by entry over the stored entries)."""
+    import torch
+    W = torch.as_tensor(np.asarray(W, np.float64), device="cuda")
+    H = torch.as_tensor(np.asarray(H, np.float64), device="cuda")
+    if P.is_csr:
+        rp = torch.as_tensor(P.rowptr, device="cuda")
+        rows = torch.repeat_interleave(torch.arange(P.m, device="cuda"), rp[1:] - rp[:-1])
+        cols = torch.as_tensor(P.colidx.astype(np.int64), device="cuda")
+        val = torch.as_tensor(P.val.astype(np.float32).astype(np.float64), device="cuda")
+        fro2 = float((val * val).sum())
+        cross = 0.0
+        for s0 in range(0, val.numel(), 1 << 20):
+            sl = slice(s0, s0 + (1 << 20))
+            cross += float((val[sl] * (W[rows[sl]] * H[:, cols[sl]].T).sum(1)).sum())
+        quad = float(((W.T @ W) * (H @ H.T)).sum())
+        return max(fro2 - 2.0 * cross + quad, 0.0) ** 0.5 / fro2 ** 0.5
+    X = torch.as_tensor(P.X.astype(np.float32), device="cuda")
+    num = den = 0.0
+    for i in range(0, P.m, 2048):
+        Xb = X[i:i + 2048].double()
+        num += float(((Xb - W[i:i + 2048] @ H) ** 2).sum())
+        den += float((Xb ** 2).sum())
+    return (num / den) ** 0.5

@@ -669,3 +669,21 @@ def test_permutation_equivariance(side):
     else:
         np.testing.assert_allclose(st.W, stp.W, rtol=1e-8, atol=1e-12)
         np.testing.assert_allclose(st.H[:, perm], stp.H, rtol=1e-8, atol=1e-12)
+
+
+def test_thread_count_does_not_change_results():
+    """The oracle's parallel loops only split independent outputs, each
+    summed in the sequential order: 1 and several threads agree bit for bit."""
+    P = wl.low_rank(130, 90, 7, seed=21, noise=0.03, dtype=np.float64)
+    out = []
+    for nt in (1, 3):
+        O.set_threads(nt)
+        p = O.Params(hp=3, lw=3, lh=4)
+        st = O.eahals_init(P.X, P.W0, P.H0, p)
+        te, _, _ = O.eahals_run(P.X, st, p, 12)
+        e2 = O.err2_direct(P.X, st.W, st.H)
+        Hn, _ = O.nnls_h(O.wtx(P.X, st.W), O.gram_w(st.W), st.H)
+        out.append((te, st.W, st.H, e2, Hn))
+    O.set_threads(0)
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
