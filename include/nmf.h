@@ -94,6 +94,11 @@ typedef struct {
                                 line-search step beta* of Sec. 3 for the
                                 W-update (a diagnostic: one more r x r product
                                 per row of W; nmf_get_line_search_trace); 0  */
+    int32_t exact_nnls;      /* 1: solve both NNLS subproblems exactly (ANLS,
+                                Sec. 1 -- with extrapolation, E-ANLS) by block
+                                principal pivoting, one warp per column of H /
+                                row of W, instead of lh / lw HALS sweeps
+                                (lw, lh, alpha unused; r <= 112); 0          */
 } nmf_params;
 
 typedef struct {
@@ -107,6 +112,10 @@ typedef struct {
     int32_t lw, lh;          /* sweep budgets in use                          */
     int32_t device_status;   /* sticky device-side status (nmf_status)        */
     int32_t launches_per_iter; /* kernels one outer iteration launches        */
+    int32_t exact_failed;    /* exact_nnls: 1 once an item's free block was not
+                                positive definite or did not settle in
+                                100 (r + 1) exchanges (the item then kept its
+                                last iterate, as the paper's solver would)    */
 } nmf_info;
 
 typedef struct {

@@ -90,6 +90,7 @@ def _load():
         "orc_line_search_beta": (ct.c_double, [vp, ct.c_int, _DP, _DP, _DP]),
         "orc_nnls": (ct.c_int, [ct.c_int, _DP, _DP, _DP, ct.c_int]),
         "orc_nnls_h": (ct.c_int, [ct.c_int64, ct.c_int, _DP, _DP, _DP]),
+        "orc_nnls_w": (ct.c_int, [ct.c_int64, ct.c_int, _DP, _DP, _DP]),
         "orc_eahals_run": (None, [vp, ct.c_int, _DP, _DP, _DP, _DP, vp, vp, ct.c_int,
                                   ct.POINTER(ct.c_int8), _DP, _DP, ct.POINTER(ct.c_uint8)]),
         "orc_ahals_run": (None, [vp, ct.c_int, _DP, _DP, ct.c_int, ct.c_int, ct.c_int, _DP]),
@@ -340,6 +341,14 @@ def nnls_h(A, G, H):
     H = _f64(H).copy()
     st = _load().orc_nnls_h(H.shape[1], H.shape[0], _ptr(A), _ptr(G), _ptr(H))
     return H, st
+
+
+def nnls_w(C, D, W):
+    """Every row of W solved exactly (warm start: W); returns (W, worst)."""
+    C, D = _f64(C), _f64(D)
+    W = _f64(W).copy()
+    st = _load().orc_nnls_w(W.shape[0], W.shape[1], _ptr(C), _ptr(D), _ptr(W))
+    return W, st
 
 
 def line_search_beta(X, W, Wn, Hy) -> float:

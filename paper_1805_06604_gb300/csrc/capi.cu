@@ -84,6 +84,7 @@ struct nmf_handle {
     float *Wn = nullptr, *Hn = nullptr, *Hw = nullptr;
     float *A = nullptr, *C = nullptr, *G = nullptr, *D = nullptr;
     float *C_lo = nullptr, *D_lo = nullptr;      // low parts for the Remark 1 terms
+    float *G_lo = nullptr;                       // exact_nnls: low part of G
     // tensor-core precision modes
     int64_t ldm = 0;                             // m rounded up to 8
     float *Wt = nullptr;                          // W_y'^T (rs x ldm), TF32
@@ -113,6 +114,7 @@ struct nmf_handle {
     unsigned char *forced = nullptr;             // decision replay (nmf_set_forced_decisions)
     int64_t forced_len = 0;
     double *eval = nullptr;                      // nmf_eval_error: e^2, e of (W, H)
+    int *nnls_status = nullptr;                  // exact_nnls: an item did not settle
     int64_t k_enq = 0;                           // iterations enqueued so far
     // graph of one iteration
     cudaGraphExec_t exec = nullptr;
@@ -132,10 +134,10 @@ void free_handle(nmf_handle *h) {
     void *ptrs[] = {h->X, h->rowptr, h->colidx, h->val, h->colptr, h->rowidx, h->cval, h->Ht,
                     h->carry,
                     h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn, h->Hw, h->A, h->C, h->G, h->D,
-                    h->C_lo, h->D_lo, h->Wt, h->Wq, h->Hq, h->Pc, h->Pc_lo, h->Pa, h->Pa_lo, h->Wth,
+                    h->C_lo, h->D_lo, h->G_lo, h->Wt, h->Wq, h->Hq, h->Pc, h->Pc_lo, h->Pa, h->Pa_lo, h->Wth,
                     h->Wtl, h->Hh, h->Hl, h->tct_c, h->tct_a, h->tc_err,
                     h->fro2, h->state, h->partials, h->counter, h->tickets, h->xtickets, h->ws, h->flag,
-                    h->tr_e, h->tr_beta, h->tr_acc, h->tr_bstar, h->forced, h->eval};
+                    h->tr_e, h->tr_beta, h->tr_acc, h->tr_bstar, h->forced, h->eval, h->nnls_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->h_state) cudaFreeHost(h->h_state);
@@ -273,7 +275,10 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
         NMF_STEP(cudaEventRecord(h->fork_ev[0], st));
         NMF_STEP(cudaStreamWaitEvent(gs, h->fork_ev[0], 0));
     }
-    NMF_STEP(launch_gram_rows(Wg, h->m, h->rs, h->r, h->rs, h->G, h->gws, gs));
+    if (h->p.exact_nnls)
+        NMF_STEP(launch_gram_rows_exact(Wg, h->m, h->rs, h->r, h->rs, h->G, h->G_lo, h->gws, gs));
+    else
+        NMF_STEP(launch_gram_rows(Wg, h->m, h->rs, h->r, h->rs, h->G, h->gws, gs));
     if (overlap) NMF_STEP(cudaEventRecord(h->join_ev[0], gs));
     NMF_STEP(mark(NMF_PHASE_WTX));
     NMF_STEP(enqueue_wtx(h, h->Wy, st));
@@ -284,7 +289,11 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
     hep.Hw = h->p.hp >= 2 ? h->Hw : nullptr;
     hep.state = h->state;
     hep.hp = h->p.hp;
-    NMF_STEP(launch_hals_h(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hy, h->Hn, h->lh, hep, st));
+    if (h->p.exact_nnls)
+        NMF_STEP(launch_nnls_h(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hy, h->Hn, hep,
+                               h->nnls_status, st));
+    else
+        NMF_STEP(launch_hals_h(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hy, h->Hn, h->lh, hep, st));
     const float *Hused = h->p.hp >= 2 ? h->Hw : h->Hn;
     NMF_STEP(mark(NMF_PHASE_GRAM_H));
     const float *Hg = nullptr;
@@ -314,7 +323,11 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
     wep.trace.forced = h->forced;
     wep.trace.forced_len = h->forced_len;
     wep.W_prev = h->p.line_search_trace ? h->W : nullptr;
-    NMF_STEP(launch_hals_w(h->m, h->r, h->rs, h->C, h->D, h->Wy, h->Wn, h->lw, wep, st));
+    if (h->p.exact_nnls)
+        NMF_STEP(launch_nnls_w(h->m, h->r, h->rs, h->C, h->D, h->Wy, h->Wn, wep, h->nnls_status,
+                               st));
+    else
+        NMF_STEP(launch_hals_w(h->m, h->r, h->rs, h->C, h->D, h->Wy, h->Wn, h->lw, wep, st));
     NMF_STEP(mark(NMF_PHASE_FINALIZE));
     NMF_STEP(launch_finalize(h->m, h->rs, h->r, h->ld, h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn,
                              h->Hw, h->state, dev_params(h), st));
@@ -398,6 +411,8 @@ nmf_status check_params(const nmf_params *p) {
     if (p->lw < 0 || p->lh < 0) return fail(NMF_EINVAL, "sweep counts must be >= 0");
     if (p->lw == 0 || p->lh == 0)
         if (!(p->alpha > 0.0)) return fail(NMF_EINVAL, "alpha must be > 0");
+    if (p->exact_nnls != 0 && p->exact_nnls != 1)
+        return fail(NMF_EINVAL, "exact_nnls must be 0 or 1 (got %d)", p->exact_nnls);
     if (p->precision < NMF_PREC_FP32 || p->precision > NMF_PREC_BF16X3)
         return fail(NMF_EINVAL, "unknown precision %d", p->precision);
     return NMF_OK;
@@ -495,6 +510,8 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     if (!X || !W0 || !H0) return fail(NMF_EINVAL, "X, W0 and H0 are required");
     if (X->m < 1 || X->n < 1 || r < 1) return fail(NMF_EINVAL, "m, n and r must be >= 1");
     if (r > kMaxRank) return fail(NMF_ENOTSUP, "r = %d exceeds the build cap %d", r, kMaxRank);
+    if (pin && pin->exact_nnls == 1 && r > 112)
+        return fail(NMF_ENOTSUP, "exact_nnls supports r <= 112 (got %d)", r);
     if (X->format != NMF_DENSE && X->format != NMF_CSR)
         return fail(NMF_EINVAL, "unknown matrix format %d", X->format);
     if (!X->values) return fail(NMF_EINVAL, "X values pointer is NULL");
@@ -573,11 +590,14 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     NMF_TRYC(dalloc(&h->G, rs * rs));
     NMF_TRYC(dalloc(&h->D, rs * rs));
     NMF_TRYC(dalloc(&h->D_lo, rs * rs));
+    NMF_TRYC(dalloc(&h->G_lo, rs * rs));
     NMF_TRYC(dalloc(&h->fro2, 1));
     NMF_TRYC(dalloc(&h->eval, 2));
+    NMF_TRYC(dalloc(&h->nnls_status, 1));
+    NMF_TRYC(cudaMemsetAsync(h->nnls_status, 0, sizeof(int), h->st));
     NMF_TRYC(dalloc(&h->state, 1));
     NMF_TRYC(dalloc(&h->flag, 1));
-    const int npart = std::max(hals_w_num_ctas(m, r), err_rows_num_ctas(m));
+    const int npart = std::max({hals_w_num_ctas(m, r), err_rows_num_ctas(m), anls_num_ctas(m)});
     NMF_TRYC(dalloc(&h->partials, npart));
     NMF_TRYC(dalloc(&h->counter, 1));
     NMF_TRYC(dalloc(&h->tickets, wtx_num_tickets(ld)));
@@ -764,6 +784,11 @@ nmf_status nmf_get_info(nmf_handle *h, nmf_info *info) {
     info->launches_per_iter = h->is_csr ? 12 : 9;
     // Tensor-core modes: + the W_y' and H_y' operand preparations.
     if (tc_mode(h)) info->launches_per_iter = 11;
+    {
+        int e = 0;
+        NMF_CUDA(cudaMemcpy(&e, h->nnls_status, sizeof(int), cudaMemcpyDeviceToHost));
+        info->exact_failed = e;
+    }
     if (h->tc_err) {
         int e = 0;
         NMF_CUDA(cudaMemcpy(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));

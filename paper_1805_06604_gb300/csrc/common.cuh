@@ -83,6 +83,11 @@ cudaError_t launch_fro2(const float *vals, int64_t rows, int64_t cols, int64_t l
 size_t gram_ws_bytes(int64_t N, int rs);
 cudaError_t launch_gram_rows(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
                              void *ws, cudaStream_t st);
+// Error-free Gram of W (G + G_lo, G the exactly rounded FP32 value): the
+// exact NNLS solves need G to FP32 accuracy, not the ~sqrt(32) u of the
+// blocked FP32 sums that the few HALS sweeps tolerate.
+cudaError_t launch_gram_rows_exact(const float *M, int64_t N, int64_t ldm, int r, int rs,
+                                   float *G, float *G_lo, void *ws, cudaStream_t st);
 // The Gram of H is accumulated error-free and returned as G + G_lo.
 cudaError_t launch_gram_cols(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
                              float *G_lo, void *ws, cudaStream_t st);
@@ -126,6 +131,18 @@ cudaError_t launch_hals_w(int64_t m, int r, int rs, const float *C, const float 
                           const float *W_in, float *W_out, int sweeps, const WEpilogue &ep,
                           cudaStream_t st);
 int hals_w_num_ctas(int64_t m, int r);
+
+// Exact NNLS subproblems (anls.cu), the block solvers of ANLS / E-ANLS:
+// same operands and epilogues as the sweeps; *status is set to 1 when an
+// item's free block was not positive definite or it did not settle (that
+// item keeps its last iterate).
+int anls_num_ctas(int64_t items);
+cudaError_t launch_nnls_h(int64_t n, int64_t ldh, int r, int rs, const float *A, const float *G,
+                          const float *H_in, float *H_out, const HEpilogue &ep, int *status,
+                          cudaStream_t st);
+cudaError_t launch_nnls_w(int64_t m, int r, int rs, const float *C, const float *D,
+                          const float *W_in, float *W_out, const WEpilogue &ep, int *status,
+                          cudaStream_t st);
 
 // Algorithm 2 steps 11-20 after the decision: extrapolation, projection and
 // accept/restart copies, W side and H side.

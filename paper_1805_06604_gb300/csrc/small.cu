@@ -451,6 +451,11 @@ cudaError_t launch_gram_rows(const float *M, int64_t N, int64_t ldm, int r, int 
     return gram_launch<true, false>(M, N, ldm, r, rs, G, nullptr, ws, st);
 }
 
+cudaError_t launch_gram_rows_exact(const float *M, int64_t N, int64_t ldm, int r, int rs,
+                                   float *G, float *G_lo, void *ws, cudaStream_t st) {
+    return gram_launch<true, true>(M, N, ldm, r, rs, G, G_lo, ws, st);
+}
+
 cudaError_t launch_gram_cols(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
                              float *G_lo, void *ws, cudaStream_t st) {
     return gram_launch<false, true>(M, N, ldm, r, rs, G, G_lo, ws, st);

@@ -98,12 +98,12 @@ def test_single_step_after_forced_restart():
     assert sc.beta_bar == pytest.approx(st.s.beta_bar, rel=1e-15)
 
 
-def _k_iterations(m, n, r, K, hp, noise):
+def _k_iterations(m, n, r, K, hp, noise, **extra):
     """K iterations on both sides from the same float32 start.  Returns the
     relative errors of the returned pairs (GPU free-running, oracle), the
     oracle's trace, and the GPU's free-running trace."""
     P = wl.low_rank(m, n, r, seed=11, noise=noise)
-    p = oracle_params(P, hp=hp)
+    p = oracle_params(P, hp=hp, **extra)
     Xo = oracle_X(P)
     st = O.eahals_init(Xo, f32(P.W0), f32(P.H0), p)
     te_o, _, ta_o = O.eahals_run(Xo, st, p, K)
@@ -116,7 +116,7 @@ def _k_iterations(m, n, r, K, hp, noise):
     return P, p, rel_g, rel_o, (te_o, ta_o), (te_g, ta_g)
 
 
-def k_iteration_parity(m, n, r, K, hp, noise):
+def k_iteration_parity(m, n, r, K, hp, noise, **extra):
     """The K-iteration gate with decision replay.  The FP32 run must take the
     oracle's accept/restart decisions except where e(k) and e(k-1) are a
     near-tie (relative gap below 1e-4 in the oracle), after which the two
@@ -124,7 +124,7 @@ def k_iteration_parity(m, n, r, K, hp, noise):
     the oracle's decisions (nmf_set_forced_decisions) and its returned pair
     must match the oracle's relative error within 1e-4 relative.  Returns
     (free-run flips, relative difference used)."""
-    P, p, rel_g, rel_o, (te_o, ta_o), (te_g, ta_g) = _k_iterations(m, n, r, K, hp, noise)
+    P, p, rel_g, rel_o, (te_o, ta_o), (te_g, ta_g) = _k_iterations(m, n, r, K, hp, noise, **extra)
     flips = np.nonzero(ta_o != ta_g)[0]
     if abs(rel_g - rel_o) <= 1e-4 * rel_o:
         return len(flips), abs(rel_g - rel_o) / rel_o
