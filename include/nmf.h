@@ -47,9 +47,13 @@ typedef enum {
 
 typedef enum { NMF_DENSE = 0, NMF_CSR = 1 } nmf_format;
 
-/* Arithmetic of the two X products (W^T X and X H^T).  Grams, sweeps and
- * extrapolation are FP32 in every mode; the error terms are accumulated in
- * FP64 (Remark 1). */
+/* Arithmetic of the two X products (W^T X and X H^T) and of the Gram
+ * G = W_y^T W_y.  In the tensor-core modes G is formed on the tensor cores
+ * from the same rounded factor W_y' as the product W_y'^T X; the Gram
+ * D = H_y H_y^T stays an error-free accumulation on the CUDA cores in every
+ * mode (Remark 1's error cancels ||X||^2 and needs D to ~2^-40).  Sweeps
+ * and extrapolation are FP32 in every mode; the error terms are accumulated
+ * in FP64 (Remark 1). */
 typedef enum {
     NMF_PREC_FP32 = 0,   /* FP32 FMA on CUDA cores                            */
     NMF_PREC_TF32 = 1,   /* TF32 tensor cores (tcgen05), FP32 accumulate; the
@@ -94,6 +98,13 @@ typedef struct {
                                 line-search step beta* of Sec. 3 for the
                                 W-update (a diagnostic: one more r x r product
                                 per row of W; nmf_get_line_search_trace); 0  */
+    double delta;            /* A-HALS inner stopping rule (Gillis & Glineur
+                                2012, cited in Sec. 1): 0 (default) runs
+                                exactly lw / lh sweeps; delta > 0 stops the
+                                loop after sweep l >= 2 once
+                                ||X^(l) - X^(l-1)||_F <= delta ||X^(1) - X^(0)||_F,
+                                lw / lh then being the caps (one launch per
+                                sweep; nmf_info reports the sweeps run)       */
     int32_t exact_nnls;      /* 1: solve both NNLS subproblems exactly (ANLS,
                                 Sec. 1 -- with extrapolation, E-ANLS) by block
                                 principal pivoting, one warp per column of H /
@@ -112,6 +123,8 @@ typedef struct {
     int32_t lw, lh;          /* sweep budgets in use                          */
     int32_t device_status;   /* sticky device-side status (nmf_status)        */
     int32_t launches_per_iter; /* kernels one outer iteration launches        */
+    int32_t lh_used, lw_used; /* sweeps on H / W in the last iteration (lh / lw
+                                unless delta > 0)                              */
     int32_t exact_failed;    /* exact_nnls: 1 once an item's free block was not
                                 positive definite or did not settle in
                                 100 (r + 1) exchanges (the item then kept its

@@ -38,13 +38,14 @@ class _Params(ct.Structure):
     _fields_ = [("hp", ct.c_int), ("beta0", ct.c_double), ("eta", ct.c_double),
                 ("gamma", ct.c_double), ("gamma_bar", ct.c_double),
                 ("lw", ct.c_int), ("lh", ct.c_int), ("project_w", ct.c_int),
-                ("compare_prev", ct.c_int), ("nnls_exact", ct.c_int)]
+                ("compare_prev", ct.c_int), ("nnls_exact", ct.c_int), ("delta", ct.c_double)]
 
 
 class _Scalars(ct.Structure):
     _fields_ = [("beta", ct.c_double), ("beta_bar", ct.c_double),
                 ("beta_prev", ct.c_double), ("e_last", ct.c_double),
-                ("e_prev", ct.c_double), ("k", ct.c_int64)]
+                ("e_prev", ct.c_double), ("k", ct.c_int64), ("lh_used", ct.c_int),
+                ("lw_used", ct.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -79,6 +80,8 @@ def _load():
         "orc_hals_col_w": (None, [ct.c_int64, ct.c_int, _DP, _DP, _DP, ct.c_int]),
         "orc_hals_sweeps_h": (None, [ct.c_int64, ct.c_int, _DP, _DP, _DP, ct.c_int]),
         "orc_hals_sweeps_w": (None, [ct.c_int64, ct.c_int, _DP, _DP, _DP, ct.c_int]),
+        "orc_hals_sweeps_h_delta": (ct.c_int, [ct.c_int64, ct.c_int, _DP, _DP, _DP, ct.c_int,
+                                               ct.c_double]),
         "orc_err2_expanded": (ct.c_double, [ct.c_double, ct.c_int64, ct.c_int, _DP, _DP, _DP]),
         "orc_err2_direct": (ct.c_double, [vp, ct.c_int, _DP, _DP]),
         "orc_sweep_counts": (None, [ct.c_int64, ct.c_int64, ct.c_int64, ct.c_int, ct.c_double,
@@ -162,10 +165,12 @@ class Params:
     project_w: int = 0
     compare_prev: int = 1        # 1: restart iff e(k) > e(k-1) (Alg. 2 step 16)
     nnls_exact: int = 0          # 1: ANLS / E-ANLS (exact NNLS subproblems)
+    delta: float = 0.0           # > 0: the A-HALS inner stopping rule
 
     def c(self) -> _Params:
         return _Params(self.hp, self.beta0, self.eta, self.gamma, self.gamma_bar,
-                       self.lw, self.lh, self.project_w, self.compare_prev, self.nnls_exact)
+                       self.lw, self.lh, self.project_w, self.compare_prev, self.nnls_exact,
+                       self.delta)
 
 
 @dataclass
@@ -176,13 +181,17 @@ class Scalars:
     e_last: float = 0.0
     e_prev: float = 0.0
     k: int = 0
+    lh_used: int = 0
+    lw_used: int = 0
 
     def c(self) -> _Scalars:
-        return _Scalars(self.beta, self.beta_bar, self.beta_prev, self.e_last, self.e_prev, self.k)
+        return _Scalars(self.beta, self.beta_bar, self.beta_prev, self.e_last, self.e_prev, self.k,
+                        self.lh_used, self.lw_used)
 
     def load(self, s: _Scalars) -> "Scalars":
         self.beta, self.beta_bar, self.beta_prev = s.beta, s.beta_bar, s.beta_prev
         self.e_last, self.e_prev, self.k = s.e_last, s.e_prev, s.k
+        self.lh_used, self.lw_used = s.lh_used, s.lw_used
         return self
 
 
@@ -247,6 +256,14 @@ def hals_sweeps_h(A, G, H, sweeps) -> np.ndarray:
     A, G, H = _f64(A), _f64(G), _f64(H).copy()
     _load().orc_hals_sweeps_h(H.shape[1], H.shape[0], _ptr(A), _ptr(G), _ptr(H), int(sweeps))
     return H
+
+
+def hals_sweeps_h_delta(A, G, H, max_sweeps, delta):
+    """A-HALS sweeps with the inner stopping rule; returns (H, sweeps done)."""
+    A, G, H = _f64(A), _f64(G), _f64(H).copy()
+    used = _load().orc_hals_sweeps_h_delta(H.shape[1], H.shape[0], _ptr(A), _ptr(G), _ptr(H),
+                                           int(max_sweeps), float(delta))
+    return H, used
 
 
 def hals_sweeps_w(C, D, W, sweeps) -> np.ndarray:

@@ -220,6 +220,55 @@ void orc_hals_sweeps_w(int64_t m, int r, const double *C, const double *D,
     }
 }
 
+/* The inner stopping rule of A-HALS (Gillis & Glineur 2012, cited in
+ * Sec. 1): sweep after sweep, ||X^(l) - X^(l-1)||_F^2 is summed over all
+ * coordinates (per column / row in index order, then the columns / rows in
+ * order) and the loop stops after sweep l >= 2 once it is at most
+ * delta^2 ||X^(1) - X^(0)||_F^2. */
+static double sq_change(const double *a, const double *b, int64_t count)
+{
+    double s = 0.0;
+    for (int64_t q = 0; q < count; ++q) {
+        const double d = a[q] - b[q];
+        s += d * d;
+    }
+    return s;
+}
+
+int orc_hals_sweeps_h_delta(int64_t n, int r, const double *A, const double *G,
+                            double *H, int max_sweeps, double delta)
+{
+    double *prev = orc_alloc((int64_t)r * n), first = 0.0;
+    int l = 0;
+    while (l < max_sweeps) {
+        memcpy(prev, H, sizeof(double) * (size_t)r * (size_t)n);
+        orc_hals_sweeps_h(n, r, A, G, H, 1);
+        ++l;
+        const double d2 = sq_change(H, prev, (int64_t)r * n);
+        if (l == 1) first = d2;
+        else if (d2 <= delta * delta * first) break;
+    }
+    free(prev);
+    return l;
+}
+
+int orc_hals_sweeps_w_delta(int64_t m, int r, const double *C, const double *D,
+                            double *W, int max_sweeps, double delta)
+{
+    double *prev = orc_alloc(m * (int64_t)r), first = 0.0;
+    int l = 0;
+    while (l < max_sweeps) {
+        memcpy(prev, W, sizeof(double) * (size_t)m * (size_t)r);
+        orc_hals_sweeps_w(m, r, C, D, W, 1);
+        ++l;
+        const double d2 = sq_change(W, prev, m * (int64_t)r);
+        if (l == 1) first = d2;
+        else if (d2 <= delta * delta * first) break;
+    }
+    free(prev);
+    return l;
+}
+
 /* Solves G_FF z = c for the free set F (Cholesky of the |F| x |F| block,
  * FP64).  F given as a list of nf indices.  Returns 0, or -1 when the block
  * is not positive definite. */
@@ -540,6 +589,7 @@ void orc_eahals_init(const orc_matrix *X, int r, const double *W,
     s->e_last = e0;
     s->e_prev = e0;
     s->k = 0;
+    s->lh_used = s->lw_used = 0;
 }
 
 /* One outer iteration of Algorithm 2 (steps 3 to 20) plus Algorithm 3. */
@@ -561,6 +611,7 @@ void orc_eahals_step(const orc_matrix *X, int r, double fro2, double *W,
     orc_gram_w(m, r, Wy, G);
     memcpy(Hn, Hy, sizeof(double) * (size_t)(r * n));
     if (p->nnls_exact) orc_nnls_h(n, r, A, G, Hn);     /* E-ANLS: exact */
+    else if (p->delta > 0.0) s->lh_used = orc_hals_sweeps_h_delta(n, r, A, G, Hn, p->lh, p->delta);
     else orc_hals_sweeps_h(n, r, A, G, Hn, p->lh);
 
     /* Steps 4-9: for hp >= 2, H_y = H_n + beta (H_n - H), projected when
@@ -581,6 +632,7 @@ void orc_eahals_step(const orc_matrix *X, int r, double fro2, double *W,
     orc_gram_h(n, r, Hw, D);
     memcpy(Wn, Wy, sizeof(double) * (size_t)(m * r));
     if (p->nnls_exact) orc_nnls_w(m, r, C, D, Wn);
+    else if (p->delta > 0.0) s->lw_used = orc_hals_sweeps_w_delta(m, r, C, D, Wn, p->lw, p->delta);
     else orc_hals_sweeps_w(m, r, C, D, Wn, p->lw);
 
     /* The line-search step of Sec. 3 for this W-update (a diagnostic). */

@@ -54,6 +54,8 @@ typedef struct {
     int nnls_exact;           /* 1: solve both NNLS subproblems exactly
                                  (ANLS, Sec. 1; with extrapolation:
                                  E-ANLS) instead of lh / lw HALS sweeps  */
+    double delta;             /* 0: exactly lh / lw sweeps; > 0: the
+                                 A-HALS stopping rule (lh / lw as caps) */
 } orc_params;
 
 typedef struct {
@@ -63,6 +65,7 @@ typedef struct {
     double e_last;            /* error the next e(k) is compared with    */
     double e_prev;            /* e(k-1) as computed (accepted or not)    */
     int64_t k;                /* iterations done                         */
+    int lh_used, lw_used;     /* sweeps the last iteration ran           */
 } orc_scalars;
 
 /* Threads used by the parallel loops (OpenMP; results do not depend on
@@ -99,6 +102,15 @@ void orc_hals_sweeps_h(int64_t n, int r, const double *A, const double *G,
                        double *H, int sweeps);
 void orc_hals_sweeps_w(int64_t m, int r, const double *C, const double *D,
                        double *W, int sweeps);
+
+/* A-HALS with the inner stopping rule of Gillis & Glineur (2012, the
+ * A-HALS paper cited in Sec. 1): after sweep l >= 2 the loop stops once
+ * ||H^(l) - H^(l-1)||_F <= delta ||H^(1) - H^(0)||_F; at most max_sweeps.
+ * Returns the number of sweeps done. */
+int orc_hals_sweeps_h_delta(int64_t n, int r, const double *A, const double *G,
+                            double *H, int max_sweeps, double delta);
+int orc_hals_sweeps_w_delta(int64_t m, int r, const double *C, const double *D,
+                            double *W, int max_sweeps, double delta);
 
 /* Exact NNLS, min_{x >= 0} 1/2 x^T G x - b^T x (G = W^T W, b = W^T v), by
  * block principal pivoting (the active-set-like method of Kim & Park that

@@ -96,6 +96,10 @@ struct nmf_handle {
     void *Pc = nullptr, *Pc_lo = nullptr, *Pa = nullptr, *Pa_lo = nullptr;
     __nv_bfloat16 *Wth = nullptr, *Wtl = nullptr, *Hh = nullptr, *Hl = nullptr;
     unsigned int *tct_c = nullptr, *tct_a = nullptr;
+    // Tensor-core Gram G = W_y'^T W_y': W_y'^T packed as P, its workspace
+    // and tile tickets.
+    void *Pg = nullptr, *Pg_lo = nullptr, *ws_g = nullptr;
+    unsigned int *tct_g = nullptr;
     int *tc_err = nullptr;
     double *fro2 = nullptr;
     DevState *state = nullptr;
@@ -115,6 +119,11 @@ struct nmf_handle {
     int64_t forced_len = 0;
     double *eval = nullptr;                      // nmf_eval_error: e^2, e of (W, H)
     int *nnls_status = nullptr;                  // exact_nnls: an item did not settle
+    // delta rule: per-sweep partials of ||change||^2 (first sweep, two
+    // alternating buffers) and the stop flags, H side then W side.
+    double *d2 = nullptr;
+    int *stopped = nullptr;
+    int np_h = 0, np_w = 0;
     int64_t k_enq = 0;                           // iterations enqueued so far
     // graph of one iteration
     cudaGraphExec_t exec = nullptr;
@@ -135,9 +144,9 @@ void free_handle(nmf_handle *h) {
                     h->carry,
                     h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn, h->Hw, h->A, h->C, h->G, h->D,
                     h->C_lo, h->D_lo, h->G_lo, h->Wt, h->Wq, h->Hq, h->Pc, h->Pc_lo, h->Pa, h->Pa_lo, h->Wth,
-                    h->Wtl, h->Hh, h->Hl, h->tct_c, h->tct_a, h->tc_err,
+                    h->Wtl, h->Hh, h->Hl, h->tct_c, h->tct_a, h->tc_err, h->Pg, h->Pg_lo, h->ws_g, h->tct_g,
                     h->fro2, h->state, h->partials, h->counter, h->tickets, h->xtickets, h->ws, h->flag,
-                    h->tr_e, h->tr_beta, h->tr_acc, h->tr_bstar, h->forced, h->eval, h->nnls_status};
+                    h->tr_e, h->tr_beta, h->tr_acc, h->tr_bstar, h->forced, h->eval, h->nnls_status, h->d2, h->stopped};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->h_state) cudaFreeHost(h->h_state);
@@ -249,6 +258,35 @@ cudaError_t enqueue_prep_h(nmf_handle *h, const float *Hsrc, cudaStream_t st, co
     return launch_tc_prep_h(Hsrc, h->r, h->ld, h->ld, h->p.precision, h->Hq, h->Hh, h->Hl, st);
 }
 
+// Tensor-core modes: G = W_y'^T W_y' on the tensor cores, from the same
+// rounded factor as the product A = W_y'^T X (W_y'^T packed as P, the
+// prepared W_y'^T as Q).  Launched without programmatic dependent launch:
+// its P changes every iteration.  (D = H_y' H_y'^T stays an error-free
+// accumulation on the CUDA cores: Remark 1's error needs it to ~2^-40.)
+cudaError_t enqueue_tc_gram(nmf_handle *h, cudaStream_t st) {
+    cudaError_t e = launch_tc_pack(h->Wq, h->m, h->r, h->rs, true, h->p.precision, h->Pg, h->Pg_lo,
+                                   st);
+    if (e != cudaSuccess) return e;
+    TcOperands o{};
+    if (h->p.precision == NMF_PREC_BF16X3) {
+        o.Q = h->Wth;
+        o.Q_lo = h->Wtl;
+    } else {
+        o.Q = h->Wt;
+    }
+    o.P = h->Pg;
+    o.P_lo = h->Pg_lo;
+    o.M = h->r;
+    o.K = h->m;
+    o.ldq = h->ldm;
+    o.q_rows = h->r;
+    o.N = round16(h->r);
+    o.nvalid = h->r;
+    o.no_pdl = 1;
+    return launch_tc_product(o, h->p.precision, false, h->G, h->rs, h->ws_g, h->tct_g, h->tc_err,
+                             st);
+}
+
 // One outer iteration of Algorithm 2, enqueued on st.  When ev != nullptr,
 // ev[i] is recorded before phase i and ev[NMF_NUM_PHASES] after the last.
 // With `overlap` (the single-instance graph), each Gram runs on the side
@@ -275,7 +313,9 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
         NMF_STEP(cudaEventRecord(h->fork_ev[0], st));
         NMF_STEP(cudaStreamWaitEvent(gs, h->fork_ev[0], 0));
     }
-    if (h->p.exact_nnls)
+    if (tc_mode(h))
+        NMF_STEP(enqueue_tc_gram(h, gs));
+    else if (h->p.exact_nnls)
         NMF_STEP(launch_gram_rows_exact(Wg, h->m, h->rs, h->r, h->rs, h->G, h->G_lo, h->gws, gs));
     else
         NMF_STEP(launch_gram_rows(Wg, h->m, h->rs, h->r, h->rs, h->G, h->gws, gs));
@@ -289,11 +329,31 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
     hep.Hw = h->p.hp >= 2 ? h->Hw : nullptr;
     hep.state = h->state;
     hep.hp = h->p.hp;
-    if (h->p.exact_nnls)
+    if (h->p.exact_nnls) {
         NMF_STEP(launch_nnls_h(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hy, h->Hn, hep,
                                h->nnls_status, st));
-    else
+    } else if (h->p.delta > 0.0) {
+        // The delta rule: one launch per sweep (each returns at once after
+        // the rule has stopped the loop), then the extrapolation epilogue.
+        NMF_STEP(cudaMemsetAsync(h->stopped, 0, sizeof(int), st));
+        double *first = h->d2, *buf = h->d2 + h->np_h;
+        for (int l = 1; l <= h->lh; ++l) {
+            HEpilogue one{};
+            one.stop.l = l;
+            one.stop.delta2 = h->p.delta * h->p.delta;
+            one.stop.d2_first = first;
+            one.stop.d2_prev = l - 1 == 1 ? first : buf + ((l - 1) & 1) * h->np_h;
+            one.stop.d2_out = l == 1 ? first : buf + (l & 1) * h->np_h;
+            one.stop.nparts = h->np_h;
+            one.stop.stopped = h->stopped;
+            one.stop.used = &h->state->lh_used;
+            NMF_STEP(launch_hals_h(h->n, h->ld, h->r, h->rs, h->A, h->G, l == 1 ? h->Hy : h->Hn,
+                                   h->Hn, 1, one, st));
+        }
+        NMF_STEP(launch_hals_h(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hn, h->Hn, 0, hep, st));
+    } else {
         NMF_STEP(launch_hals_h(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hy, h->Hn, h->lh, hep, st));
+    }
     const float *Hused = h->p.hp >= 2 ? h->Hw : h->Hn;
     NMF_STEP(mark(NMF_PHASE_GRAM_H));
     const float *Hg = nullptr;
@@ -323,11 +383,29 @@ cudaError_t enqueue_iteration(nmf_handle *h, cudaStream_t st, cudaEvent_t *ev = 
     wep.trace.forced = h->forced;
     wep.trace.forced_len = h->forced_len;
     wep.W_prev = h->p.line_search_trace ? h->W : nullptr;
-    if (h->p.exact_nnls)
+    if (h->p.exact_nnls) {
         NMF_STEP(launch_nnls_w(h->m, h->r, h->rs, h->C, h->D, h->Wy, h->Wn, wep, h->nnls_status,
                                st));
-    else
+    } else if (h->p.delta > 0.0) {
+        NMF_STEP(cudaMemsetAsync(h->stopped + 1, 0, sizeof(int), st));
+        double *first = h->d2 + 3 * h->np_h, *buf = first + h->np_w;
+        for (int l = 1; l <= h->lw; ++l) {
+            WEpilogue one{};
+            one.stop.l = l;
+            one.stop.delta2 = h->p.delta * h->p.delta;
+            one.stop.d2_first = first;
+            one.stop.d2_prev = l - 1 == 1 ? first : buf + ((l - 1) & 1) * h->np_w;
+            one.stop.d2_out = l == 1 ? first : buf + (l & 1) * h->np_w;
+            one.stop.nparts = h->np_w;
+            one.stop.stopped = h->stopped + 1;
+            one.stop.used = &h->state->lw_used;
+            NMF_STEP(launch_hals_w(h->m, h->r, h->rs, h->C, h->D, l == 1 ? h->Wy : h->Wn, h->Wn, 1,
+                                   one, st));
+        }
+        NMF_STEP(launch_hals_w(h->m, h->r, h->rs, h->C, h->D, h->Wn, h->Wn, 0, wep, st));
+    } else {
         NMF_STEP(launch_hals_w(h->m, h->r, h->rs, h->C, h->D, h->Wy, h->Wn, h->lw, wep, st));
+    }
     NMF_STEP(mark(NMF_PHASE_FINALIZE));
     NMF_STEP(launch_finalize(h->m, h->rs, h->r, h->ld, h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn,
                              h->Hw, h->state, dev_params(h), st));
@@ -411,6 +489,8 @@ nmf_status check_params(const nmf_params *p) {
     if (p->lw < 0 || p->lh < 0) return fail(NMF_EINVAL, "sweep counts must be >= 0");
     if (p->lw == 0 || p->lh == 0)
         if (!(p->alpha > 0.0)) return fail(NMF_EINVAL, "alpha must be > 0");
+    if (!(p->delta >= 0.0) || !(p->delta < 1.0))
+        return fail(NMF_EINVAL, "delta must lie in [0, 1) (got %g)", p->delta);
     if (p->exact_nnls != 0 && p->exact_nnls != 1)
         return fail(NMF_EINVAL, "exact_nnls must be 0 or 1 (got %d)", p->exact_nnls);
     if (p->precision < NMF_PREC_FP32 || p->precision > NMF_PREC_BF16X3)
@@ -594,6 +674,10 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
     NMF_TRYC(dalloc(&h->fro2, 1));
     NMF_TRYC(dalloc(&h->eval, 2));
     NMF_TRYC(dalloc(&h->nnls_status, 1));
+    h->np_h = hals_h_num_ctas(n, r);
+    h->np_w = hals_w_num_ctas(m, r);
+    NMF_TRYC(dalloc(&h->d2, 3 * (size_t)(h->np_h + h->np_w)));
+    NMF_TRYC(dalloc(&h->stopped, 2));
     NMF_TRYC(cudaMemsetAsync(h->nnls_status, 0, sizeof(int), h->st));
     NMF_TRYC(dalloc(&h->state, 1));
     NMF_TRYC(dalloc(&h->flag, 1));
@@ -715,6 +799,14 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
             NMF_TRYC(dalloc(&h->tct_c, tc_num_tickets(m)));
             NMF_TRYC(dalloc(&h->tct_a, tc_num_tickets(n)));
             NMF_TRYC(dalloc(&h->tc_err, 1));
+            {
+                const size_t bg = tc_packed_bytes(r, m, p.precision);
+                NMF_TRYC(cudaMalloc(&h->Pg, bg));
+                if (p.precision == NMF_PREC_BF16X3) NMF_TRYC(cudaMalloc(&h->Pg_lo, bg));
+                NMF_TRYC(cudaMalloc(&h->ws_g, tc_ws_bytes(r, m, round16(r), p.precision)));
+                NMF_TRYC(dalloc(&h->tct_g, tc_num_tickets(r)));
+                NMF_TRYC(cudaMemsetAsync(h->tct_g, 0, sizeof(unsigned int) * tc_num_tickets(r), st));
+            }
             NMF_TRYC(cudaMemsetAsync(h->tct_c, 0, sizeof(unsigned int) * tc_num_tickets(m), st));
             NMF_TRYC(cudaMemsetAsync(h->tct_a, 0, sizeof(unsigned int) * tc_num_tickets(n), st));
             NMF_TRYC(cudaMemsetAsync(h->tc_err, 0, sizeof(int), st));
@@ -782,8 +874,11 @@ nmf_status nmf_get_info(nmf_handle *h, nmf_info *info) {
     // W sweeps (1) + finalize (1); CSR: each product is 2 kernels (+ a
     // memset) and X H^T adds the H transpose.
     info->launches_per_iter = h->is_csr ? 12 : 9;
+    info->lh_used = h->p.delta > 0.0 ? d.lh_used : (h->p.exact_nnls ? 0 : h->lh);
+    info->lw_used = h->p.delta > 0.0 ? d.lw_used : (h->p.exact_nnls ? 0 : h->lw);
     // Tensor-core modes: + the W_y' and H_y' operand preparations.
     if (tc_mode(h)) info->launches_per_iter = 11;
+    if (h->p.delta > 0.0 && !h->p.exact_nnls) info->launches_per_iter += h->lh + h->lw;
     {
         int e = 0;
         NMF_CUDA(cudaMemcpy(&e, h->nnls_status, sizeof(int), cudaMemcpyDeviceToHost));

@@ -28,6 +28,7 @@ struct DevState {
     long long k;          // iterations done
     int accepted;         // decision of the last iteration
     int status;           // sticky nmf_status raised on the device
+    int lh_used, lw_used; // inner sweeps the last iteration ran (delta rule)
 };
 
 // Parameters the device logic needs (copied by value into kernel args).
@@ -106,6 +107,25 @@ cudaError_t launch_xht_f32(const float *X, int64_t m, int64_t ldx, int r, const 
                            int64_t ldh, float *C, float *C_lo, int rs, void *ws,
                            unsigned int *tickets, cudaStream_t st);
 
+// The early stop of A-HALS's inner loop (Gillis & Glineur 2012): sweep l
+// runs only while the previous one still moved the iterate by more than
+// delta times the first one, ||X^(l-1) - X^(l-2)||_F > delta ||X^(1) - X^(0)||_F.
+// In that mode every sweep is one launch (sweeps = 1, l = 1, 2, ...); each
+// sums ||change||^2 over its CTA into d2_out[CTA], and launch l >= 3 first
+// compares the totals of sweeps l-1 and 1 (every CTA adds the partials in
+// the same fixed order, so all take the same decision) and, once the rule
+// holds, sets *stopped and every later launch returns at once.
+struct SweepStop {
+    int l;                    // 1-based sweep of this launch; 0: rule off
+    double delta2;            // delta^2
+    const double *d2_first;   // partials of sweep 1
+    const double *d2_prev;    // partials of sweep l-1
+    double *d2_out;           // partials of this sweep, one per CTA
+    int nparts;               // CTAs per launch
+    int *stopped;             // 1 once the rule has stopped the loop
+    int *used;                // sweeps done this iteration
+};
+
 // HALS sweeps.  H side: columns of H independent given A and G.  W side:
 // rows of W independent given C and D.
 struct HEpilogue {            // optional fused work after the H sweeps
@@ -113,6 +133,7 @@ struct HEpilogue {            // optional fused work after the H sweeps
     float *Hw;                // where to write the H_y used by the W-update, or null
     const DevState *state;    // beta_k
     int hp;
+    SweepStop stop;
 };
 struct WEpilogue {            // optional fused work after the W sweeps
     const float *C_lo;        // low parts of C = X H^T and D = H H^T (error terms)
@@ -123,6 +144,7 @@ struct WEpilogue {            // optional fused work after the W sweeps
     DevParams params;
     DevTrace trace;
     const float *W_prev;      // the accepted W (line-search diagnostic), or null
+    SweepStop stop;
 };
 cudaError_t launch_hals_h(int64_t n, int64_t ldh, int r, int rs, const float *A,
                           const float *G, const float *H_in, float *H_out, int sweeps,
@@ -131,6 +153,7 @@ cudaError_t launch_hals_w(int64_t m, int r, int rs, const float *C, const float 
                           const float *W_in, float *W_out, int sweeps, const WEpilogue &ep,
                           cudaStream_t st);
 int hals_w_num_ctas(int64_t m, int r);
+int hals_h_num_ctas(int64_t n, int r);
 
 // Exact NNLS subproblems (anls.cu), the block solvers of ANLS / E-ANLS:
 // same operands and epilogues as the sweeps; *status is set to 1 when an
@@ -192,6 +215,9 @@ struct TcOperands {
     const void *P, *P_lo, *Q, *Q_lo;
     int64_t M, K, ldq;
     int q_rows, N, nvalid;
+    int no_pdl;         // 1: plain launch.  With programmatic dependent launch
+                        // the kernel streams P before its predecessor ends,
+                        // which is only right when P is constant (packed X).
 };
 size_t tc_packed_bytes(int64_t M, int64_t K, int precision);
 cudaError_t launch_tc_pack(const float *x, int64_t rows, int64_t cols, int64_t ld, bool transposed,

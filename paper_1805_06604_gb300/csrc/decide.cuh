@@ -48,4 +48,54 @@ __device__ __forceinline__ void decide_and_update_beta(DevState *s, const DevPar
     s->k = k + 1;
 }
 
+// Sum of p[0..n) in a fixed order by the whole CTA (blockDim.x a multiple
+// of 32, <= 1024): thread t adds p[t], p[t + blockDim], ... in order, the
+// warps combine by a fixed butterfly, and warp sums are added in warp order.
+// Every CTA that calls it on the same data gets the same bits.
+__device__ __forceinline__ double cta_sum_fixed(const double *p, int n, double *sh32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += p[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (threadIdx.x % 32 == 0) sh32[threadIdx.x / 32] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += sh32[w];
+    __syncthreads();
+    return s;
+}
+
+// The early-stop test at the start of sweep launch l (see SweepStop):
+// true when this launch must not sweep.  Uniform across the CTA.
+__device__ __forceinline__ bool sweep_stopped(const SweepStop &st, double *sh32) {
+    if (st.l <= 0) return false;
+    if (*(volatile int *)st.stopped) return true;
+    if (st.l < 3) return false;
+    const double prev = cta_sum_fixed(st.d2_prev, st.nparts, sh32);
+    const double first = cta_sum_fixed(st.d2_first, st.nparts, sh32);
+    if (prev <= st.delta2 * first) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) *st.stopped = 1;
+        return true;
+    }
+    return false;
+}
+
+// The sum of squared changes of this CTA's items after sweep l, and the
+// sweep count.  v is the thread's own partial.
+__device__ __forceinline__ void sweep_record(const SweepStop &st, double v, double *sh32) {
+    if (st.l <= 0) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (threadIdx.x % 32 == 0) sh32[threadIdx.x / 32] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += sh32[w];
+        st.d2_out[blockIdx.x] = s;
+        if (blockIdx.x == 0) *st.used = st.l;
+    }
+}
+
 }  // namespace nmfg

@@ -128,7 +128,7 @@ hals_kernel(int64_t items, int r, int64_t ld,
             const float *__restrict__ Aglob,     // right-hand side a (A or C)
             const float *__restrict__ Gglob,     // Gram (G or D), rs x rs
             int rs,
-            const float *__restrict__ Xin, float *__restrict__ Xout, int sweeps,
+            const float *Xin, float *Xout, int sweeps,     // may alias (one sweep in place)
             int hoist_guard, HEpilogue hep, WEpilogue wep) {
     constexpr int RP = S * T;                    // padded item length
     constexpr int D = T;                         // lookahead depth
@@ -145,7 +145,10 @@ hals_kernel(int64_t items, int r, int64_t ld,
     __shared__ double red_cross[kThreads / 32], red_quad[kThreads / 32];
     __shared__ double red_bnum[kThreads / 32], red_bden[kThreads / 32];
     __shared__ bool am_last;
+    __shared__ double sh32[32];
     const bool err_terms = LAYOUT == kRow && wep.partials != nullptr;
+    const SweepStop &stop = LAYOUT == kRow ? wep.stop : hep.stop;
+    if (sweep_stopped(stop, sh32)) return;               // A-HALS early stop (delta rule)
     // A programmatically dependent successor (the tensor-core X product)
     // may start streaming X now; it waits for this grid before reading H_y.
     asm volatile("griddepcontrol.launch_dependents;");
@@ -312,11 +315,20 @@ hals_kernel(int64_t items, int r, int64_t ld,
 
     // Keeps the compiler from moving the stores into the sweep loop.
     asm volatile("" ::: "memory");
+    double moved = 0.0;                                  // ||change||^2 (delta rule)
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         const int k = s * T + t;
-        if (valid && k < r) Xout[elem_index<LAYOUT>(item, k, ld)] = x[s];
+        if (valid && k < r) {
+            const int64_t q = elem_index<LAYOUT>(item, k, ld);
+            if (stop.l > 0) {
+                const double dx = (double)x[s] - (double)Xin[q];
+                moved = fma(dx, dx, moved);
+            }
+            Xout[q] = x[s];
+        }
     }
+    sweep_record(stop, moved, sh32);
 
     if constexpr (LAYOUT == kColumn) {
         // Algorithm 2 steps 4-9: H_y = H_n + beta (H_n - H), projected if hp = 3.

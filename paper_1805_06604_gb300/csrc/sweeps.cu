@@ -39,6 +39,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "decide.cuh"
 
 namespace nmfg {
 namespace {
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kThreads)
 sweep_kernel(int64_t items, int r, int64_t ld, int nt,
              const float *__restrict__ Aglob,     // right-hand side a (A or C)
              const float *__restrict__ Gglob,     // Gram (G or D), rs x rs
-             int rs, const float *__restrict__ Xin, float *__restrict__ Xout, int sweeps,
+             int rs, const float *Xin, float *Xout, int sweeps,   // may alias (one sweep in place)
              HEpilogue hep) {
     // A programmatically dependent successor (the tensor-core X product)
     // may start streaming X now; it waits for this grid before reading H_y.
@@ -125,6 +126,8 @@ sweep_kernel(int64_t items, int r, int64_t ld, int nt,
     const int64_t item0 = (int64_t)blockIdx.x * nt;
     const int nhere = (int)(items - item0 < (int64_t)nt ? items - item0 : (int64_t)nt);
     const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+    __shared__ double sh32[32];
+    if (sweep_stopped(hep.stop, sh32)) return;         // A-HALS early stop (delta rule)
 
     for (int e = tid; e < rp * rp; e += kThreads) {
         const int k = e / rp, i = e % rp;
@@ -273,6 +276,7 @@ sweep_kernel(int64_t items, int r, int64_t ld, int nt,
     __syncthreads();
 
     // ---------------------------------------------------- results
+    double moved = 0.0;                                 // ||change||^2 (delta rule)
     for (int e = tid; e < rp * kItems; e += kThreads) {
         int k, j;
         if (LAYOUT == kColumn) {
@@ -285,6 +289,10 @@ sweep_kernel(int64_t items, int r, int64_t ld, int nt,
         if (j < nhere && k < r) {
             const int64_t q = elem_index<LAYOUT>(item0 + j, k, ld);
             const float x = xs[j * rps + k];
+            if (hep.stop.l > 0) {
+                const double dx = (double)x - (double)Xin[q];
+                moved = fma(dx, dx, moved);
+            }
             Xout[q] = x;
             if (LAYOUT == kColumn && hep.Hw != nullptr) {
                 // Algorithm 2 steps 4-9: H_y = H_n + beta (H_n - H), projected if hp = 3.
@@ -295,6 +303,7 @@ sweep_kernel(int64_t items, int r, int64_t ld, int nt,
             }
         }
     }
+    sweep_record(hep.stop, moved, sh32);
 
 }
 
@@ -337,6 +346,12 @@ cudaError_t sweep_launch(int64_t items, int r, int64_t ld, const float *A, const
 }
 
 }  // namespace
+
+int hals_h_num_ctas(int64_t n, int r) {
+    (void)r;
+    const int nt = items_per_cta(n);
+    return (int)((n + nt - 1) / nt);
+}
 
 cudaError_t launch_hals_h(int64_t n, int64_t ldh, int r, int rs, const float *A,
                           const float *G, const float *H_in, float *H_out, int sweeps,

@@ -818,7 +818,7 @@ cudaError_t tc_launch(const TcOperands &o, float *out, int64_t out_ld, void *ws,
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = o.no_pdl ? 0 : 1;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<const unsigned char *>(o.P),
                               static_cast<const unsigned char *>(o.P_lo), mq, mql, o.M, p.tiles,
                               p.nk, o.nvalid, out, out_ld, static_cast<float *>(ws), p.seg_max,

@@ -41,7 +41,7 @@ class nmf_params(ct.Structure):
                 ("lh", ct.c_int32), ("alpha", ct.c_double), ("project_w", ct.c_int32),
                 ("compare_prev", ct.c_int32), ("precision", ct.c_int32),
                 ("trace_capacity", ct.c_int64), ("line_search_trace", ct.c_int32),
-                ("exact_nnls", ct.c_int32)]
+                ("delta", ct.c_double), ("exact_nnls", ct.c_int32)]
 
 
 class nmf_info(ct.Structure):
@@ -49,7 +49,8 @@ class nmf_info(ct.Structure):
                 ("fro2", ct.c_double), ("relerr", ct.c_double), ("beta", ct.c_double),
                 ("beta_bar", ct.c_double), ("beta_prev", ct.c_double), ("accepted", ct.c_int32),
                 ("lw", ct.c_int32), ("lh", ct.c_int32), ("device_status", ct.c_int32),
-                ("launches_per_iter", ct.c_int32), ("exact_failed", ct.c_int32)]
+                ("launches_per_iter", ct.c_int32), ("lh_used", ct.c_int32),
+                ("lw_used", ct.c_int32), ("exact_failed", ct.c_int32)]
 
 
 class nmf_result(ct.Structure):

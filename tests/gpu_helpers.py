@@ -49,19 +49,20 @@ def normwise(a, b) -> float:
 
 
 def oracle_params(P, hp=3, beta0=0.5, eta=1.5, gamma=1.01, gamma_bar=1.005, project_w=0,
-                  compare_prev=1, lw=None, lh=None, nnls_exact=0):
+                  compare_prev=1, lw=None, lh=None, nnls_exact=0, delta=0.0):
     if lw is None or lh is None:
         aw, ah = O.sweep_counts(P.m, P.n, P.nnz, P.r)
         lw = aw if lw is None else lw
         lh = ah if lh is None else lh
     return O.Params(hp=hp, beta0=beta0, eta=eta, gamma=gamma, gamma_bar=gamma_bar, lw=lw, lh=lh,
-                    project_w=project_w, compare_prev=compare_prev, nnls_exact=nnls_exact)
+                    project_w=project_w, compare_prev=compare_prev, nnls_exact=nnls_exact,
+                    delta=delta)
 
 
 def gpu_kwargs(p: O.Params) -> dict:
     return dict(hp=p.hp, beta0=p.beta0, eta=p.eta, gamma=p.gamma, gamma_bar=p.gamma_bar,
                 lw=p.lw, lh=p.lh, project_w=p.project_w, compare_prev=p.compare_prev,
-                exact_nnls=p.nnls_exact)
+                exact_nnls=p.nnls_exact, delta=p.delta)
 
 
 def oracle_X(P):

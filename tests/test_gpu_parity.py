@@ -458,3 +458,35 @@ def test_line_search_diagnostic_matches_oracle(m, n, r, hp, warm, csr):
     print(f"\nbeta*: gpu {bs_gpu:.9f} oracle-at-gpu-iterates {bs_mixed:.9f} oracle {bs_orc:.9f}")
     assert abs(bs_gpu - bs_mixed) <= 1e-5 * (1.0 + abs(bs_mixed))
     assert abs(bs_gpu - bs_orc) <= 1e-3
+
+
+@pytest.mark.parametrize("delta", [0.1, 0.3])
+def test_delta_rule_single_step(delta):
+    """The A-HALS inner stopping rule (nmf_params.delta): from an identical
+    state the GPU stops the H and W loops after the same number of sweeps as
+    the oracle, and the step matches within the FP32 step gate."""
+    from gpu_helpers import load_state, state_to_f32
+    P = wl.low_rank(300, 220, 12, seed=41, noise=0.02)
+    p = oracle_params(P, delta=delta)
+    Xo = oracle_X(P)
+    st = O.eahals_init(Xo, P.W0.astype(np.float32), P.H0.astype(np.float32), p)
+    O.eahals_run(Xo, st, p, 3)
+    st = state_to_f32(st)
+    from gpu_helpers import gram_kappa, step_tol
+    kappa = gram_kappa(st)
+    with make_solver(P, p) as s:
+        load_state(s, st)
+        info = s.step(1, last=True)
+        _, W, H, Wy, Hy = s.get_state()
+    e_o, _, acc_o = O.eahals_step(Xo, st, p)
+    print(f"\ndelta {delta}: sweeps H {info.lh_used} / {st.s.lh_used}, "
+          f"W {info.lw_used} / {st.s.lw_used} (caps {p.lh}, {p.lw})")
+    assert (info.lh_used, info.lw_used) == (st.s.lh_used, st.s.lw_used)
+    assert info.lh_used < p.lh or info.lw_used < p.lw
+    assert bool(info.accepted) == acc_o
+    for a, b in ((W, st.W), (H, st.H), (Wy, st.Wy), (Hy, st.Hy)):
+        assert normwise(a, b) <= step_tol(kappa)
+
+
+def test_delta_rule_k_iterations():
+    k_iteration_parity(300, 200, 8, 400, 3, 0.05, delta=0.1)

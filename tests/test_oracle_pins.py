@@ -687,3 +687,49 @@ def test_thread_count_does_not_change_results():
     O.set_threads(0)
     for a, b in zip(out[0], out[1]):
         np.testing.assert_array_equal(a, b)
+
+
+# ------------------------------------------- A-HALS inner stopping rule
+
+@pytest.mark.parametrize("delta", [1e-12, 0.5, 0.1, 0.01])
+def test_delta_rule_stops_where_the_definition_says(delta):
+    """orc_hals_sweeps_h_delta against the rule of Gillis & Glineur (2012)
+    evaluated with numpy on single sweeps: stop after the first sweep l >= 2
+    with ||H^(l) - H^(l-1)||_F <= delta ||H^(1) - H^(0)||_F (cap 30), and
+    the result equals that many plain sweeps bit for bit."""
+    P = wl.low_rank(60, 40, 6, seed=30, noise=0.05, dtype=np.float64)
+    W = _rand((60, 6), 31)
+    A, G = O.wtx(P.X, W), O.gram_w(W)
+    H0 = _rand((6, 40), 32)
+    Hd, used = O.hals_sweeps_h_delta(A, G, H0, 30, delta)
+    H = H0.copy()
+    first, want = None, 30
+    for l in range(1, 31):
+        Hn = O.hals_sweeps_h(A, G, H, 1)
+        d = np.linalg.norm(Hn - H)
+        H = Hn
+        if l == 1:
+            first = d
+        elif d <= delta * first:
+            want = l
+            break
+    assert used == want
+    np.testing.assert_array_equal(Hd, O.hals_sweeps_h(A, G, H0, used))
+    if delta >= 0.5:
+        assert used < 30
+    if delta == 1e-12:
+        assert used == 30
+
+
+def test_delta_rule_in_the_step_reports_its_sweeps():
+    P = wl.low_rank(50, 40, 5, seed=33, noise=0.05, dtype=np.float64)
+    p = O.Params(hp=3, lw=20, lh=25, delta=0.1)
+    st = O.eahals_init(P.X, P.W0, P.H0, p)
+    O.eahals_step(P.X, st, p)
+    assert 2 <= st.s.lh_used <= 25 and 2 <= st.s.lw_used <= 20
+    # the same step with fixed counts equal to those sweeps is identical
+    q = O.Params(hp=3, lw=st.s.lw_used, lh=st.s.lh_used)
+    s2 = O.eahals_init(P.X, P.W0, P.H0, q)
+    O.eahals_step(P.X, s2, q)
+    np.testing.assert_array_equal(st.W, s2.W)
+    np.testing.assert_array_equal(st.H, s2.H)
