@@ -229,7 +229,44 @@ def other_workloads(nmf, torch, stream):
         t = timed_steps(sv, 300, stream)
         doc[name] = {"iters_per_s": 300 / t, "relerr": sv.info().relerr}
         sv.close()
+    # The CSR products against HBM (stored entries: 4 B value + 4 B index
+    # per nonzero, read once per product) and the factor rows they gather
+    # (r floats per nonzero, served mostly from L2).
+    sv = nmf.Solver(None, P.r, P.W0.astype(np.float32), P.H0.astype(np.float32), csr=csr,
+                    m=P.m, n=P.n, stream=stream)
+    sv.step(3)
+    pm = sv.profile_phases(10)
+    sv.close()
+    hbm_gbs = peaks()[0]
+    nnz = float(P.nnz)
+    for k in ("wtx", "xht"):
+        s_ = pm[k] / 1000.0
+        stored = 8.0 * nnz + 4.0 * P.r * (P.m + P.n)
+        gathered = 4.0 * P.r * nnz
+        doc[k] = {"us": pm[k] * 1000.0, "stored_gbs": stored / s_ / 1e9,
+                  "frac_of_hbm": stored / s_ / 1e9 / hbm_gbs,
+                  "gathered_gbs": gathered / s_ / 1e9}
     out["document_like_csr"] = doc
+    # E-ANLS (exact NNLS subproblems, nmf_params.exact_nnls) and the A-HALS
+    # inner stopping rule (delta = 0.1) on the dense noisy workload.
+    Pd = wl.dense_noisy(0)
+    Xd = torch.from_numpy(Pd.X).cuda()
+    W0d, H0d = torch.from_numpy(Pd.W0).cuda(), torch.from_numpy(Pd.H0).cuda()
+    extra = {}
+    for name, kw, steps in (("eanls", {"exact_nnls": 1}, 50), ("delta_0.1", {"delta": 0.1}, 100)):
+        sv = nmf.Solver(Xd, Pd.r, W0d, H0d, stream=stream, **kw)
+        sv.step(3)
+        t = timed_steps(sv, steps, stream)
+        info = sv.info()
+        ent = {"iters_per_s": steps / t, "steps": steps, "relerr_pair": sv.eval_error()[1],
+               "sweeps_last_iter": [int(info.lh_used), int(info.lw_used)],
+               "exact_failed": int(info.exact_failed)}
+        ph = sv.profile_phases(3)
+        ent["phase_us"] = {k: v * 1000.0 for k, v in ph.items()}
+        extra[name] = ent
+        sv.close()
+    out["dense_noisy_variants"] = extra
+    del Xd, W0d, H0d
     # The parameter study of Sec. 4.2 (reduced: one data set, two
     # initialisations, all 109 variants in batched graphs).
     from paper_1805_06604_gb300 import sweep

@@ -315,17 +315,13 @@ sweep_kernel(int64_t items, int r, int64_t ld, int nt,
 // for the H side).
 constexpr int kBlockH = 8;
 
-// Items per CTA: at most 32 (one per lane of the chain warp), as few as
-// keep all items on one wave of CTAs per SM group.  A CTA's time is set by
-// its chain warp, whatever its item count, so the items are spread evenly
-// over the smallest number of CTA "rounds" per SM that holds them.
+// Items per CTA: 32, one per lane of the chain warp.  A CTA's time is set
+// by its chain warp whatever its item count, so full CTAs leave the most SMs
+// to other work (the batched solver runs many instances side by side; dense
+// 4000 columns: 125 CTAs of 32 take as long as 149 of 27).
 int items_per_cta(int64_t items) {
-    const int64_t rounds = (items + (int64_t)kNumSMs * kItems - 1) / ((int64_t)kNumSMs * kItems);
-    const int64_t ctas = rounds * kNumSMs;
-    int64_t nt = (items + ctas - 1) / ctas;
-    if (nt < 1) nt = 1;
-    if (nt > kItems) nt = kItems;
-    return (int)nt;
+    (void)items;
+    return kItems;
 }
 
 template <int LAYOUT, int B>
