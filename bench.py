@@ -202,7 +202,6 @@ def other_workloads(nmf, torch, stream):
     # Batched: 512 uneven instances, one graph per iteration vs a launch loop.
     probs = wl.batch(count=512, seed=0)
     b = nmf.Batch([(Q.X, Q.r, Q.W0, Q.H0) for Q in probs])
-    branches, tuned = b.schedule()
     res = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for name, fn in (("graph", b.step), ("loop", b.step_loop)):
@@ -213,9 +212,23 @@ def other_workloads(nmf, torch, stream):
         e1.record()
         torch.cuda.synchronize()
         res[name] = e0.elapsed_time(e1) / 20.0
+    pl = b.plan()
+    plan = {"grouped": pl.grouped, "branches": pl.branches, "h_cols_per_cta": pl.h_cols_per_cta,
+            "launches_per_iter": pl.launches_per_iter}
+    if pl.grouped:
+        # The per-instance chains on 64 branches, for comparison.
+        b.set_plan(0, 64, 0)
+        b.step(1)
+        torch.cuda.synchronize()
+        e0.record()
+        b.step(20)
+        e1.record()
+        torch.cuda.synchronize()
+        res["chains_64"] = e0.elapsed_time(e1) / 20.0
     b.close()
-    out["batched_512"] = {"instances": 512, "branches": branches,
+    out["batched_512"] = {"instances": 512, "plan": plan,
                           "graph_ms_per_iter": res["graph"], "loop_ms_per_iter": res["loop"],
+                          "chains_graph_ms_per_iter": res.get("chains_64"),
                           "speedup": res["loop"] / res["graph"],
                           "instance_iters_per_s": 512 * 1000.0 / res["graph"]}
     # Document-like CSR 50000 x 20000, r = 30: E-A-HALS and A-HALS.

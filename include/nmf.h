@@ -337,12 +337,33 @@ nmf_status nmf_fro2_noalloc(const float *X, int64_t m, int64_t n, int64_t ld,
 
 /* ---- Batched solver: many independent problems of uneven size. ---------
  * Each instance is a full solver (as nmf_create).  One outer iteration of
- * every instance is captured into a single CUDA graph in which the
- * instances form independent chains spread over B concurrent branches; the
- * number of branches and the longest-first assignment of instances to
- * branches are picked at creation by timing candidate graphs (the tuning
- * iterations are undone from a device snapshot).  All work goes on `stream`. */
+ * every instance is captured into a single CUDA graph, in one of two forms:
+ *  - grouped: one launch per phase of Algorithm 2 and kernel variant covers
+ *    all instances (a device table gives every CTA its instance and its
+ *    index within it), so an iteration of hundreds of instances is a few
+ *    dozen launches; available when every instance is dense, FP32, without
+ *    the delta rule and without exact NNLS;
+ *  - chains: every instance's own kernels form a chain, and the chains are
+ *    spread over B concurrent graph branches (longest first).
+ * Both forms run each instance's kernels with the tiles, splits and CTAs of
+ * its single solver, so results are bit-identical to nmf_step on that
+ * instance.  The form, the branches, and the grouped form's columns of H
+ * per sweep CTA are picked at creation by timing candidate graphs (the
+ * tuning iterations are undone from a device snapshot).  All work goes on
+ * `stream`. */
 typedef struct nmf_batch nmf_batch;
+
+/* A schedule of the batched graph. */
+typedef struct nmf_batch_plan {
+    int32_t grouped;           /* 1: grouped launches, 0: per-instance chains   */
+    int32_t branches;          /* chains: concurrent branches (1..64); grouped:
+                                  branches the launches of one phase are spread
+                                  over (1..64)                                   */
+    int32_t h_cols_per_cta;    /* grouped: columns of H per CTA of the H sweeps
+                                  (1..32; 0 = the single solver's 32)            */
+    int32_t launches_per_iter; /* out: kernel launches per outer iteration      */
+    double ms_per_iter;        /* out: measured by the tuner (0 if set by hand) */
+} nmf_batch_plan;
 
 /* Xs[i], ranks[i], W0[i] (m_i x r_i), H0[i] (r_i x n_i) describe instance
  * i; p applies to all (sweep budgets computed per instance when 0).
@@ -371,6 +392,13 @@ nmf_status nmf_batch_get_factors(nmf_batch *b, int32_t i, float *W, float *H,
                                  int32_t to_device);
 /* The autotuner's choice: branches and its measured ms per iteration. */
 nmf_status nmf_batch_schedule(nmf_batch *b, int32_t *branches, double *ms_per_iter);
+/* The schedule in use (all fields). */
+nmf_status nmf_batch_get_plan(nmf_batch *b, nmf_batch_plan *plan);
+/* Rebuilds the graph with the given schedule (grouped, branches,
+ * h_cols_per_cta; the out fields are ignored).  Errors: NMF_EINVAL for NULL
+ * or out-of-range fields, NMF_ENOTSUP for grouped when an instance is not
+ * dense FP32 HALS, NMF_ECUDA for capture failures. */
+nmf_status nmf_batch_set_plan(nmf_batch *b, const nmf_batch_plan *plan);
 nmf_status nmf_batch_destroy(nmf_batch *b);
 
 /* Message of the last failing call on this thread ("" if none). */

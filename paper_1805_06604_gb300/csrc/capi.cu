@@ -1236,8 +1236,8 @@ struct nmf_batch {
     std::vector<nmf_handle *> h;
     std::vector<cudaStream_t> br;               // capture streams
     cudaGraphExec_t exec = nullptr;
-    int branches = 1;
-    double tuned_ms = 0.0;
+    void *tables = nullptr;                     // device tables of a grouped graph
+    nmf_batch_plan plan{};                      // schedule of `exec`
     int64_t k_enq = 0;
 };
 
@@ -1246,6 +1246,7 @@ namespace {
 void free_batch(nmf_batch *b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->tables) cudaFree(b->tables);
     for (auto *h : b->h) free_handle(h);
     for (auto s : b->br) cudaStreamDestroy(s);
     delete b;
@@ -1273,7 +1274,7 @@ std::vector<std::vector<int>> assign(const nmf_batch *b, int branches) {
     return out;
 }
 
-nmf_status build_batch_graph(nmf_batch *b, int branches, cudaGraphExec_t *exec) {
+nmf_status build_chains_graph(nmf_batch *b, int branches, cudaGraphExec_t *exec) {
     *exec = nullptr;
     const auto groups = assign(b, branches);
     cudaStream_t origin = b->br[0];
@@ -1313,6 +1314,302 @@ nmf_status build_batch_graph(nmf_batch *b, int branches, cudaGraphExec_t *exec) 
     e = cudaGraphInstantiate(exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(NMF_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    return NMF_OK;
+}
+
+
+// ---------------------------------------------------------------- grouped
+// One outer iteration of all instances as a few grouped launches, phase by
+// phase of Algorithm 2: [Gram of W_y | A = W_y^T X] -> H sweeps -> [Gram of
+// H_y | C = X H_y^T] -> W sweeps with the error and the decision ->
+// finalize.  Within a phase, the launches of the different kernel variants
+// (instances of different r) are independent and may run on concurrent
+// branches.  Every instance gets exactly the CTAs of its single launch.
+bool batch_groupable(const nmf_batch *b) {
+    for (auto *h : b->h)
+        if (h->is_csr || h->p.precision != NMF_PREC_FP32 || h->p.delta > 0.0 || h->p.exact_nnls ||
+            hals_w_group_key(h->m, h->r) < 0)
+            return false;
+    return true;
+}
+
+enum GKind { kGramPartial, kGramReduce, kWtx, kSweepH, kXht, kHalsW, kFinalize };
+struct GLaunch {
+    GKind kind;
+    int key;
+    size_t items, begin;        // byte offsets into the device tables
+    int nitems;
+    int64_t ctas;
+    int max_r;
+};
+
+struct GStaging {
+    std::vector<unsigned char> host;
+    size_t add(const void *p, size_t bytes) {
+        const size_t off = (host.size() + 15) / 16 * 16;
+        host.resize(off + bytes);
+        memcpy(host.data() + off, p, bytes);
+        return off;
+    }
+};
+
+// Items of one kernel variant (key) in instance order of decreasing cost,
+// so that the largest instances' CTAs are dispatched first.
+template <typename Item>
+GLaunch stage_group(GStaging &sg, GKind kind, int key, const std::vector<Item> &items,
+                    const std::vector<int64_t> &ctas, int max_r) {
+    std::vector<int64_t> begin(items.size() + 1, 0);
+    for (size_t i = 0; i < items.size(); ++i) begin[i + 1] = begin[i] + ctas[i];
+    GLaunch L{};
+    L.kind = kind;
+    L.key = key;
+    L.items = sg.add(items.data(), sizeof(Item) * items.size());
+    L.begin = sg.add(begin.data(), sizeof(int64_t) * begin.size());
+    L.nitems = (int)items.size();
+    L.ctas = begin.back();
+    L.max_r = max_r;
+    return L;
+}
+
+cudaError_t run_glaunch(const GLaunch &L, const unsigned char *dev, cudaStream_t st) {
+    const int64_t *begin = reinterpret_cast<const int64_t *>(dev + L.begin);
+    const void *items = dev + L.items;
+    switch (L.kind) {
+        case kGramPartial:
+            return launch_gram_partial_grouped(L.key, static_cast<const GramItem *>(items), begin,
+                                               L.nitems, L.ctas, st);
+        case kGramReduce:
+            return launch_gram_reduce_grouped((L.key & 1) != 0,
+                                              static_cast<const GramItem *>(items), begin,
+                                              L.nitems, L.ctas, st);
+        case kWtx:
+            return launch_wtx_grouped(L.key, static_cast<const WtxItem *>(items), begin, L.nitems,
+                                      L.ctas, st);
+        case kSweepH:
+            return launch_sweep_h_grouped(static_cast<const SweepItem *>(items), begin, L.nitems,
+                                          L.ctas, L.max_r, st);
+        case kXht:
+            return launch_xht_grouped(L.key, static_cast<const XhtItem *>(items), begin, L.nitems,
+                                      L.ctas, st);
+        case kHalsW:
+            return launch_hals_w_grouped(L.key, static_cast<const HalsWItem *>(items), begin,
+                                         L.nitems, L.ctas, st);
+        case kFinalize:
+            return launch_finalize_grouped(static_cast<const FinalizeItem *>(items), begin,
+                                           L.nitems, L.ctas, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+using GChain = std::vector<GLaunch>;        // launches in order on one branch
+using GPhase = std::vector<GChain>;         // independent chains
+
+// Groups the instances by key (in order of decreasing cost) and stages one
+// launch -- or a partial + reduce chain for the Grams -- per key.
+template <typename Item, typename Plan>
+void stage_phase(GStaging &sg, GPhase &ph, const nmf_batch *b, const std::vector<int> &order,
+                 GKind kind, Plan plan) {
+    std::vector<int> keys;
+    std::vector<std::vector<Item>> items;
+    std::vector<std::vector<int64_t>> ctas, ctas2;
+    std::vector<int> max_r;
+    for (int i : order) {
+        Item it{};
+        int64_t c = 0, c2 = 0;
+        const int key = plan(b->h[i], &it, &c, &c2);
+        size_t g = std::find(keys.begin(), keys.end(), key) - keys.begin();
+        if (g == keys.size()) {
+            keys.push_back(key);
+            items.push_back(std::vector<Item>());
+            ctas.push_back(std::vector<int64_t>());
+            ctas2.push_back(std::vector<int64_t>());
+            max_r.push_back(0);
+        }
+        items[g].push_back(it);
+        ctas[g].push_back(c);
+        ctas2[g].push_back(c2);
+        max_r[g] = std::max(max_r[g], b->h[i]->r);
+    }
+    for (size_t g = 0; g < keys.size(); ++g) {
+        GChain ch;
+        ch.push_back(stage_group(sg, kind, keys[g], items[g], ctas[g], max_r[g]));
+        if (kind == kGramPartial) {
+            GLaunch red = stage_group(sg, kGramReduce, keys[g], items[g], ctas2[g],
+                                      max_r[g]);
+            ch.push_back(red);
+        }
+        ph.push_back(ch);
+    }
+}
+
+nmf_status build_grouped_graph(nmf_batch *b, int branches, int h_cols, cudaGraphExec_t *exec,
+                               void **tables, int *launches) {
+    *exec = nullptr;
+    *tables = nullptr;
+    std::vector<int> order(b->h.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return est_cost(b->h[x]) > est_cost(b->h[y]); });
+    GStaging sg;
+    std::vector<GPhase> phases(5);
+    cudaError_t ce = cudaSuccess;
+    auto keep = [&](cudaError_t e) {
+        if (e != cudaSuccess && ce == cudaSuccess) ce = e;
+    };
+    // Phase 1: G = W_y^T W_y (FP32 Gram) beside A = W_y^T X.
+    stage_phase<GramItem>(sg, phases[0], b, order, kGramPartial,
+                          [&](nmf_handle *h, GramItem *it, int64_t *c, int64_t *c2) {
+                              plan_gram_item(h->Wy, h->m, h->rs, h->r, h->rs, h->G, nullptr,
+                                             h->gws, it, c, c2);
+                              return gram_group_key(h->r, true, false);
+                          });
+    stage_phase<WtxItem>(sg, phases[0], b, order, kWtx,
+                         [&](nmf_handle *h, WtxItem *it, int64_t *c, int64_t *) {
+                             keep(plan_wtx_item(h->X, h->m, h->ld, h->ld, h->r, h->Wy, h->rs,
+                                                h->A, h->ws, h->tickets, it, c));
+                             return wtx_group_key(h->rs);
+                         });
+    // Phase 2: the H sweeps with the fused extrapolation of H (steps 3-9).
+    stage_phase<SweepItem>(sg, phases[1], b, order, kSweepH,
+                           [&](nmf_handle *h, SweepItem *it, int64_t *c, int64_t *) {
+                               HEpilogue hep{};
+                               hep.H_acc = h->H;
+                               hep.Hw = h->p.hp >= 2 ? h->Hw : nullptr;
+                               hep.state = h->state;
+                               hep.hp = h->p.hp;
+                               plan_sweep_h_item(h->n, h->ld, h->r, h->rs, h->A, h->G, h->Hy,
+                                                 h->Hn, h->lh, hep, h_cols, it, c);
+                               return 0;
+                           });
+    // Phase 3: D = H_y H_y^T (error-free) beside C = X H_y^T.
+    stage_phase<GramItem>(sg, phases[2], b, order, kGramPartial,
+                          [&](nmf_handle *h, GramItem *it, int64_t *c, int64_t *c2) {
+                              const float *Hu = h->p.hp >= 2 ? h->Hw : h->Hn;
+                              plan_gram_item(Hu, h->n, h->ld, h->r, h->rs, h->D, h->D_lo, h->gws,
+                                             it, c, c2);
+                              return gram_group_key(h->r, false, true);
+                          });
+    stage_phase<XhtItem>(sg, phases[2], b, order, kXht,
+                         [&](nmf_handle *h, XhtItem *it, int64_t *c, int64_t *) {
+                             const float *Hu = h->p.hp >= 2 ? h->Hw : h->Hn;
+                             keep(plan_xht_item(h->X, h->m, h->ld, h->r, Hu, h->ld, h->C, h->C_lo,
+                                                h->rs, h->ws, h->xtickets, it, c));
+                             return xht_group_key(h->m, h->r);
+                         });
+    // Phase 4: the W sweeps, Remark 1's error, the decision (steps 10, 15-20).
+    stage_phase<HalsWItem>(sg, phases[3], b, order, kHalsW,
+                           [&](nmf_handle *h, HalsWItem *it, int64_t *c, int64_t *) {
+                               WEpilogue wep{};
+                               wep.C_lo = h->C_lo;
+                               wep.D_lo = h->D_lo;
+                               wep.partials = h->partials;
+                               wep.counter = h->counter;
+                               wep.state = h->state;
+                               wep.params = dev_params(h);
+                               wep.trace.e = h->tr_e;
+                               wep.trace.beta = h->tr_beta;
+                               wep.trace.acc = h->tr_acc;
+                               wep.trace.cap = h->tr_cap;
+                               wep.trace.bstar = h->tr_bstar;
+                               wep.trace.forced = h->forced;
+                               wep.trace.forced_len = h->forced_len;
+                               wep.W_prev = h->p.line_search_trace ? h->W : nullptr;
+                               plan_hals_w_item(h->m, h->r, h->rs, h->C, h->D, h->Wy, h->Wn,
+                                                h->lw, wep, it, c);
+                               return hals_w_group_key(h->m, h->r);
+                           });
+    // Phase 5: extrapolation of W (and of H for hp = 1), accept/restart copies.
+    stage_phase<FinalizeItem>(sg, phases[4], b, order, kFinalize,
+                              [&](nmf_handle *h, FinalizeItem *it, int64_t *c, int64_t *) {
+                                  plan_finalize_item(h->m, h->rs, h->r, h->ld, h->W, h->H, h->Wy,
+                                                     h->Hy, h->Wn, h->Hn, h->Hw, h->state,
+                                                     dev_params(h), it, c);
+                                  return 0;
+                              });
+    if (ce != cudaSuccess) return fail(NMF_ECUDA, "grouped plan: %s", cudaGetErrorString(ce));
+
+    void *dev = nullptr;
+    NMF_CUDA(cudaMalloc(&dev, std::max<size_t>(sg.host.size(), 16)));
+    cudaError_t e = cudaMemcpy(dev, sg.host.data(), sg.host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        return fail(NMF_ECUDA, "grouped tables: %s", cudaGetErrorString(e));
+    }
+    const unsigned char *d = static_cast<const unsigned char *>(dev);
+    cudaStream_t origin = b->br[0];
+    const int nb = std::max(1, std::min(branches, (int)b->br.size()));
+    cudaGraph_t g = nullptr;
+    std::vector<cudaEvent_t> evs;
+    auto mk = [&]() {
+        cudaEvent_t ev;
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        evs.push_back(ev);
+        return ev;
+    };
+    int count = 0;
+    e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    for (const GPhase &ph : phases) {
+        if (e != cudaSuccess) break;
+        const int used = std::min<int>(nb, (int)ph.size());
+        if (used > 1) {
+            cudaEvent_t fork = mk();
+            e = cudaEventRecord(fork, origin);
+            for (int j = 1; j < used && e == cudaSuccess; ++j)
+                e = cudaStreamWaitEvent(b->br[j], fork, 0);
+        }
+        for (size_t c = 0; c < ph.size() && e == cudaSuccess; ++c)
+            for (const GLaunch &L : ph[c]) {
+                e = run_glaunch(L, d, b->br[c % used]);
+                ++count;
+                if (e != cudaSuccess) break;
+            }
+        for (int j = 1; j < used && e == cudaSuccess; ++j) {
+            cudaEvent_t join = mk();
+            e = cudaEventRecord(join, b->br[j]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, join, 0);
+        }
+    }
+    cudaError_t e2 = cudaStreamEndCapture(origin, &g);
+    for (auto ev : evs) cudaEventDestroy(ev);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        cudaFree(dev);
+        return fail(NMF_ECUDA, "grouped graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        return fail(NMF_ECUDA, "grouped graph instantiate: %s", cudaGetErrorString(e));
+    }
+    *tables = dev;
+    *launches = count;
+    return NMF_OK;
+}
+
+// Builds the graph of a schedule; on success it replaces b's graph.
+nmf_status build_batch_graph(nmf_batch *b, const nmf_batch_plan &pl) {
+    cudaGraphExec_t ex = nullptr;
+    void *tab = nullptr;
+    int launches = 0;
+    nmf_status s;
+    if (pl.grouped) {
+        s = build_grouped_graph(b, pl.branches, pl.h_cols_per_cta, &ex, &tab, &launches);
+    } else {
+        s = build_chains_graph(b, pl.branches, &ex);
+        launches = 0;
+        for (auto *h : b->h) launches += h->is_csr ? 12 : (tc_mode(h) ? 11 : 9);
+    }
+    if (s != NMF_OK) return s;
+    NMF_CUDA(cudaStreamSynchronize(b->st));          // the old graph may still run
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->tables) cudaFree(b->tables);
+    b->exec = ex;
+    b->tables = tab;
+    b->plan = pl;
+    b->plan.launches_per_iter = launches;
     return NMF_OK;
 }
 
@@ -1358,19 +1655,49 @@ nmf_status batch_ensure_trace(nmf_batch *b, int64_t need) {
             grown = true;
         }
     if (grown && b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-        nmf_status s = build_batch_graph(b, b->branches, &b->exec);
+        nmf_status s = build_batch_graph(b, b->plan);
         if (s != NMF_OK) return s;
     }
     return NMF_OK;
 }
 
+// Times `iters` graph launches of a candidate schedule (after one warm-up).
+nmf_status time_plan(nmf_batch *b, const nmf_batch_plan &pl, cudaEvent_t e0, cudaEvent_t e1,
+                     double *ms) {
+    cudaGraphExec_t ex = nullptr;
+    void *tab = nullptr;
+    int launches = 0;
+    nmf_status s = pl.grouped ? build_grouped_graph(b, pl.branches, pl.h_cols_per_cta, &ex, &tab,
+                                                    &launches)
+                              : build_chains_graph(b, pl.branches, &ex);
+    if (s != NMF_OK) return s;
+    cudaGraphLaunch(ex, b->st);                 // warm
+    cudaEventRecord(e0, b->st);
+    for (int it = 0; it < 3; ++it) cudaGraphLaunch(ex, b->st);
+    cudaEventRecord(e1, b->st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaGraphExecDestroy(ex);
+    if (tab) cudaFree(tab);
+    if (e != cudaSuccess) return fail(NMF_ECUDA, "autotune run failed: %s", cudaGetErrorString(e));
+    *ms = t / 3.0;
+    return NMF_OK;
+}
+
+// Candidate schedules: chains over 1..64 branches; grouped launches (when
+// every instance allows them) with the launches of a phase on one or on
+// several branches, and 32 or 16 columns of H per sweep CTA.  The fastest
+// measured one is kept.
 nmf_status autotune(nmf_batch *b) {
     const int count = (int)b->h.size();
-    std::vector<int> cands;
+    std::vector<nmf_batch_plan> cands;
     for (int c : {1, 2, 4, 8, 16, 32, 64})
-        if (c <= count && c <= (int)b->br.size()) cands.push_back(c);
+        if (c <= count && c <= (int)b->br.size()) cands.push_back(nmf_batch_plan{0, c, 0, 0, 0.0});
+    if (batch_groupable(b))
+        for (int c : {1, 16})
+            for (int cols : {32, 16})
+                if (c <= (int)b->br.size()) cands.push_back(nmf_batch_plan{1, c, cols, 0, 0.0});
     nmf_status s = batch_ensure_trace(b, b->k_enq + 4 * (int64_t)cands.size() + 8);
     if (s != NMF_OK) return s;
     Snapshot sn;
@@ -1380,26 +1707,14 @@ nmf_status autotune(nmf_batch *b) {
     NMF_CUDA(cudaEventCreate(&e0));
     NMF_CUDA(cudaEventCreate(&e1));
     double best = 1e30;
-    int best_c = 1;
-    for (int c : cands) {
-        cudaGraphExec_t ex = nullptr;
-        s = build_batch_graph(b, c, &ex);
+    nmf_batch_plan best_pl = cands.front();
+    for (const auto &pl : cands) {
+        double ms = 0.0;
+        s = time_plan(b, pl, e0, e1, &ms);
         if (s != NMF_OK) break;
-        cudaGraphLaunch(ex, b->st);                 // warm
-        cudaEventRecord(e0, b->st);
-        for (int it = 0; it < 3; ++it) cudaGraphLaunch(ex, b->st);
-        cudaEventRecord(e1, b->st);
-        cudaError_t e = cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-        cudaGraphExecDestroy(ex);
-        if (e != cudaSuccess) {
-            s = fail(NMF_ECUDA, "autotune run failed: %s", cudaGetErrorString(e));
-            break;
-        }
-        if (ms / 3.0 < best) {
-            best = ms / 3.0;
-            best_c = c;
+        if (ms < best) {
+            best = ms;
+            best_pl = pl;
         }
     }
     cudaEventDestroy(e0);
@@ -1407,9 +1722,10 @@ nmf_status autotune(nmf_batch *b) {
     if (s != NMF_OK) return s;
     s = snapshot(b, sn, true);                      // undo the tuning iterations
     if (s != NMF_OK) return s;
-    b->branches = best_c;
-    b->tuned_ms = best;
-    return build_batch_graph(b, best_c, &b->exec);
+    s = build_batch_graph(b, best_pl);
+    if (s != NMF_OK) return s;
+    b->plan.ms_per_iter = best;
+    return NMF_OK;
 }
 
 }  // namespace
@@ -1511,9 +1827,28 @@ nmf_status nmf_batch_get_factors(nmf_batch *b, int32_t i, float *W, float *H, in
 
 nmf_status nmf_batch_schedule(nmf_batch *b, int32_t *branches, double *ms_per_iter) {
     if (!b) return fail(NMF_EINVAL, "batch is NULL");
-    if (branches) *branches = b->branches;
-    if (ms_per_iter) *ms_per_iter = b->tuned_ms;
+    if (branches) *branches = b->plan.branches;
+    if (ms_per_iter) *ms_per_iter = b->plan.ms_per_iter;
     return NMF_OK;
+}
+
+nmf_status nmf_batch_get_plan(nmf_batch *b, nmf_batch_plan *plan) {
+    if (!b || !plan) return fail(NMF_EINVAL, "batch or plan is NULL");
+    *plan = b->plan;
+    return NMF_OK;
+}
+
+nmf_status nmf_batch_set_plan(nmf_batch *b, const nmf_batch_plan *plan) {
+    if (!b || !plan) return fail(NMF_EINVAL, "batch or plan is NULL");
+    nmf_batch_plan pl = *plan;
+    if ((pl.grouped != 0 && pl.grouped != 1) || pl.branches < 1 || pl.branches > 64 ||
+        pl.h_cols_per_cta < 0 || pl.h_cols_per_cta > 32)
+        return fail(NMF_EINVAL, "plan fields out of range");
+    if (pl.grouped && !batch_groupable(b))
+        return fail(NMF_ENOTSUP, "grouped launches need dense FP32 HALS instances");
+    pl.branches = std::min<int>(pl.branches, (int)b->br.size());
+    pl.ms_per_iter = 0.0;
+    return build_batch_graph(b, pl);
 }
 
 nmf_status nmf_batch_destroy(nmf_batch *b) {

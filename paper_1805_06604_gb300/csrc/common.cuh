@@ -107,6 +107,100 @@ cudaError_t launch_xht_f32(const float *X, int64_t m, int64_t ldx, int r, const 
                            int64_t ldh, float *C, float *C_lo, int rs, void *ws,
                            unsigned int *tickets, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Grouped launches (the batched solver): one launch runs one kernel variant
+// over many independent problems.  Each problem is an item of a device
+// table holding its own arguments and CTA count; CTA b of the launch serves
+// the item i with begin[i] <= b < begin[i + 1], as its CTA b - begin[i].  An
+// item thus runs exactly the CTAs, tiles and splits of its own single
+// launch, and computes the same values bit for bit.
+// ---------------------------------------------------------------------------
+// The item of this CTA of a grouped launch (binary search of the prefix
+// sums) and the CTA's index within the item.
+__device__ __forceinline__ int group_item(const int64_t *__restrict__ begin, int nitems,
+                                          int64_t &local) {
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = nitems - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(begin + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    local = b - __ldg(begin + lo);
+    return lo;
+}
+
+struct WtxItem {
+    const float *X;
+    int64_t m, ldx;
+    int r;
+    const float *W;
+    float *A;
+    int64_t lda, rows_per_split;
+    float *part;
+    unsigned int *tickets;
+    int64_t tiles;
+    int nsplit;
+};
+struct XhtItem {
+    const float *X;
+    int64_t m, ldx;
+    int r;
+    const float *H;
+    int64_t ldh;
+    float *C, *C_lo;
+    int rs;
+    int64_t cols_per_split;
+    float *part;
+    unsigned int *tickets;
+    int64_t tiles;
+    int nsplit;
+};
+// A Gram (launch_gram_rows / launch_gram_cols): partial launch, then reduce.
+struct GramItem {
+    const float *M;
+    int64_t N, ldm;
+    int r, rs;
+    int64_t chunk;
+    float *part, *part_lo;
+    int nparts;
+    float *G, *G_lo;
+};
+struct FinalizeItem {
+    int64_t nw, nh;
+    float *W, *H, *Wy, *Hy;
+    const float *Wn, *Hn, *Hw;
+    const DevState *state;
+    DevParams p;
+};
+// Item setup: the variant key (items of one key share a launch), the item's
+// arguments and its CTA count(s).
+int gram_group_key(int r, bool rows, bool exact);
+void plan_gram_item(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
+                    float *G_lo, void *ws, GramItem *it, int64_t *ctas_partial,
+                    int64_t *ctas_reduce);
+cudaError_t launch_gram_partial_grouped(int key, const GramItem *items, const int64_t *begin,
+                                        int nitems, int64_t ctas, cudaStream_t st);
+cudaError_t launch_gram_reduce_grouped(bool exact, const GramItem *items, const int64_t *begin,
+                                       int nitems, int64_t ctas, cudaStream_t st);
+void plan_finalize_item(int64_t m, int rs, int r, int64_t ldh, float *W, float *H, float *Wy,
+                        float *Hy, const float *Wn, const float *Hn, const float *Hw,
+                        const DevState *state, DevParams p, FinalizeItem *it, int64_t *ctas);
+cudaError_t launch_finalize_grouped(const FinalizeItem *items, const int64_t *begin, int nitems,
+                                    int64_t ctas, cudaStream_t st);
+int wtx_group_key(int rs);
+cudaError_t plan_wtx_item(const float *X, int64_t m, int64_t lda, int64_t ldx, int r,
+                          const float *W, int rs, float *A, void *ws, unsigned int *tickets,
+                          WtxItem *it, int64_t *ctas);
+cudaError_t launch_wtx_grouped(int key, const WtxItem *items, const int64_t *begin, int nitems,
+                               int64_t ctas, cudaStream_t st);
+int xht_group_key(int64_t m, int r);
+cudaError_t plan_xht_item(const float *X, int64_t m, int64_t ldx, int r, const float *H,
+                          int64_t ldh, float *C, float *C_lo, int rs, void *ws,
+                          unsigned int *tickets, XhtItem *it, int64_t *ctas);
+cudaError_t launch_xht_grouped(int key, const XhtItem *items, const int64_t *begin, int nitems,
+                               int64_t ctas, cudaStream_t st);
+
 // The early stop of A-HALS's inner loop (Gillis & Glineur 2012): sweep l
 // runs only while the previous one still moved the iterate by more than
 // delta times the first one, ||X^(l-1) - X^(l-2)||_F > delta ||X^(1) - X^(0)||_F.
@@ -146,6 +240,43 @@ struct WEpilogue {            // optional fused work after the W sweeps
     const float *W_prev;      // the accepted W (line-search diagnostic), or null
     SweepStop stop;
 };
+// Grouped sweeps (see the grouped launches above).  H side: the blocked
+// kernel; W side: the lane-pipelined kernel, whose variant key is (T, S).
+struct SweepItem {
+    int64_t items;
+    int r;
+    int64_t ld;
+    int nt;
+    const float *A, *G;
+    int rs;
+    const float *Xin;
+    float *Xout;
+    int sweeps;
+    HEpilogue hep;
+};
+struct HalsWItem {
+    int64_t items;
+    int r;
+    int64_t ld;
+    const float *A, *G;
+    int rs;
+    const float *Xin;
+    float *Xout;
+    int sweeps;
+    WEpilogue wep;
+    int64_t nblk;            // CTAs of the item (its error partials)
+};
+void plan_sweep_h_item(int64_t n, int64_t ldh, int r, int rs, const float *A, const float *G,
+                       const float *H_in, float *H_out, int sweeps, const HEpilogue &ep, int nt,
+                       SweepItem *it, int64_t *ctas);
+cudaError_t launch_sweep_h_grouped(const SweepItem *items, const int64_t *begin, int nitems,
+                                   int64_t ctas, int max_r, cudaStream_t st);
+int hals_w_group_key(int64_t m, int r);      // -1: no grouped variant
+void plan_hals_w_item(int64_t m, int r, int rs, const float *C, const float *D,
+                      const float *W_in, float *W_out, int sweeps, const WEpilogue &ep,
+                      HalsWItem *it, int64_t *ctas);
+cudaError_t launch_hals_w_grouped(int key, const HalsWItem *items, const int64_t *begin,
+                                  int nitems, int64_t ctas, cudaStream_t st);
 cudaError_t launch_hals_h(int64_t n, int64_t ldh, int r, int rs, const float *A,
                           const float *G, const float *H_in, float *H_out, int sweeps,
                           const HEpilogue &ep, cudaStream_t st);

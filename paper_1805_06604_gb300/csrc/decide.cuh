@@ -67,15 +67,16 @@ __device__ __forceinline__ double cta_sum_fixed(const double *p, int n, double *
 }
 
 // The early-stop test at the start of sweep launch l (see SweepStop):
-// true when this launch must not sweep.  Uniform across the CTA.
-__device__ __forceinline__ bool sweep_stopped(const SweepStop &st, double *sh32) {
+// true when this launch must not sweep.  Uniform across the CTA.  bid: the
+// CTA's index in its launch.
+__device__ __forceinline__ bool sweep_stopped(const SweepStop &st, double *sh32, int64_t bid) {
     if (st.l <= 0) return false;
     if (*(volatile int *)st.stopped) return true;
     if (st.l < 3) return false;
     const double prev = cta_sum_fixed(st.d2_prev, st.nparts, sh32);
     const double first = cta_sum_fixed(st.d2_first, st.nparts, sh32);
     if (prev <= st.delta2 * first) {
-        if (threadIdx.x == 0 && blockIdx.x == 0) *st.stopped = 1;
+        if (threadIdx.x == 0 && bid == 0) *st.stopped = 1;
         return true;
     }
     return false;
@@ -83,7 +84,8 @@ __device__ __forceinline__ bool sweep_stopped(const SweepStop &st, double *sh32)
 
 // The sum of squared changes of this CTA's items after sweep l, and the
 // sweep count.  v is the thread's own partial.
-__device__ __forceinline__ void sweep_record(const SweepStop &st, double v, double *sh32) {
+__device__ __forceinline__ void sweep_record(const SweepStop &st, double v, double *sh32,
+                                             int64_t bid) {
     if (st.l <= 0) return;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -93,8 +95,8 @@ __device__ __forceinline__ void sweep_record(const SweepStop &st, double v, doub
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += sh32[w];
-        st.d2_out[blockIdx.x] = s;
-        if (blockIdx.x == 0) *st.used = st.l;
+        st.d2_out[bid] = s;
+        if (bid == 0) *st.used = st.l;
     }
 }
 

@@ -123,13 +123,14 @@ __device__ __forceinline__ float group_allreduce(float p) {
 }
 
 template <int T, int S, int LAYOUT>
-__global__ void __launch_bounds__(kThreads, 1)
-hals_kernel(int64_t items, int r, int64_t ld,
-            const float *__restrict__ Aglob,     // right-hand side a (A or C)
-            const float *__restrict__ Gglob,     // Gram (G or D), rs x rs
-            int rs,
-            const float *Xin, float *Xout, int sweeps,     // may alias (one sweep in place)
-            int hoist_guard, HEpilogue hep, WEpilogue wep) {
+__device__ __forceinline__ void
+hals_body(int64_t items, int r, int64_t ld,
+          const float *__restrict__ Aglob,     // right-hand side a (A or C)
+          const float *__restrict__ Gglob,     // Gram (G or D), rs x rs
+          int rs,
+          const float *Xin, float *Xout, int sweeps,     // may alias (one sweep in place)
+          int hoist_guard, const HEpilogue &hep, const WEpilogue &wep,
+          int64_t bid, int64_t nblk) {     // CTA index and count of the launch (or item)
     constexpr int RP = S * T;                    // padded item length
     constexpr int D = T;                         // lookahead depth
     constexpr int PF = 2;                        // prefetch distance (updates)
@@ -148,7 +149,7 @@ hals_kernel(int64_t items, int r, int64_t ld,
     __shared__ double sh32[32];
     const bool err_terms = LAYOUT == kRow && wep.partials != nullptr;
     const SweepStop &stop = LAYOUT == kRow ? wep.stop : hep.stop;
-    if (sweep_stopped(stop, sh32)) return;               // A-HALS early stop (delta rule)
+    if (sweep_stopped(stop, sh32, bid)) return;          // A-HALS early stop (delta rule)
     // A programmatically dependent successor (the tensor-core X product)
     // may start streaming X now; it waits for this grid before reading H_y.
     asm volatile("griddepcontrol.launch_dependents;");
@@ -184,7 +185,7 @@ hals_kernel(int64_t items, int r, int64_t ld,
     __syncthreads();
 
     const int t = threadIdx.x % T;
-    const int64_t item = (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T;
+    const int64_t item = bid * (blockDim.x / T) + threadIdx.x / T;
     const bool valid = item < items;
     const unsigned gmask = 0xffffffffu;
 
@@ -328,7 +329,7 @@ hals_kernel(int64_t items, int r, int64_t ld,
             Xout[q] = x[s];
         }
     }
-    sweep_record(stop, moved, sh32);
+    sweep_record(stop, moved, sh32, bid);
 
     if constexpr (LAYOUT == kColumn) {
         // Algorithm 2 steps 4-9: H_y = H_n + beta (H_n - H), projected if hp = 3.
@@ -430,20 +431,20 @@ hals_kernel(int64_t items, int r, int64_t ld,
                 bn += red_bnum[w];
                 bd += red_bden[w];
             }
-            wep.partials[blockIdx.x].cross = c;
-            wep.partials[blockIdx.x].quad = qd;
-            wep.partials[blockIdx.x].bnum = bn;
-            wep.partials[blockIdx.x].bden = bd;
+            wep.partials[bid].cross = c;
+            wep.partials[bid].quad = qd;
+            wep.partials[bid].bnum = bn;
+            wep.partials[bid].bden = bd;
             __threadfence();
             const unsigned int done = atomicAdd(wep.counter, 1u);
-            am_last = (done == gridDim.x - 1);
+            am_last = (done == (unsigned int)(nblk - 1));
         }
         __syncthreads();
         if (am_last) {
             // Fixed-order sum of the CTA partials (deterministic).
             __threadfence();
             double c = 0.0, qd = 0.0, bn = 0.0, bd = 0.0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+            for (int b = threadIdx.x; b < (int)nblk; b += blockDim.x) {
                 const volatile ErrPartial *pp = wep.partials + b;
                 c += pp->cross;
                 qd += pp->quad;
@@ -477,6 +478,26 @@ hals_kernel(int64_t items, int r, int64_t ld,
     }
 }
 
+template <int T, int S, int LAYOUT>
+__global__ void __launch_bounds__(kThreads, 1)
+hals_kernel(int64_t items, int r, int64_t ld, const float *__restrict__ Aglob,
+            const float *__restrict__ Gglob, int rs, const float *Xin, float *Xout, int sweeps,
+            int hoist_guard, HEpilogue hep, WEpilogue wep) {
+    hals_body<T, S, LAYOUT>(items, r, ld, Aglob, Gglob, rs, Xin, Xout, sweeps, hoist_guard, hep,
+                            wep, blockIdx.x, gridDim.x);
+}
+// W side of many problems in one launch (hoist_guard: 0, as above).
+template <int T, int S>
+__global__ void __launch_bounds__(kThreads, 1)
+hals_w_grouped(const HalsWItem *__restrict__ table, const int64_t *__restrict__ begin,
+               int nitems, int hoist_guard) {
+    int64_t local;
+    const HalsWItem &it = table[group_item(begin, nitems, local)];
+    const HEpilogue none{};
+    hals_body<T, S, kRow>(it.items, it.r, it.ld, it.A, it.G, it.rs, it.Xin, it.Xout, it.sweeps,
+                          hoist_guard, none, it.wep, local, it.nblk);
+}
+
 }  // namespace
 
 // Launches the sweep kernel for T lanes per item and S slots per lane.
@@ -502,12 +523,33 @@ cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const 
     return cudaGetLastError();
 }
 
+// A grouped launch of the W side (all items share T, S and the CTA size).
+template <int T, int S>
+cudaError_t hals_w_launch_grouped(const HalsWItem *items, const int64_t *begin, int nitems,
+                                  int64_t ctas, int cta_threads, cudaStream_t st) {
+    constexpr int RP = S * T;
+    constexpr int SP = 4 * ((S + 3) / 4) + (((S + 3) / 4) % 2 == 0 ? 4 : 0);
+    const size_t smem = sizeof(float) * (size_t)(RP * T * SP * 2 + RP * 16);
+    auto kern = hals_w_grouped<T, S>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (cta_threads < 32 || cta_threads > kThreads || cta_threads % 32) return cudaErrorInvalidValue;
+    if (nitems < 1 || ctas < 1) return cudaSuccess;
+    kern<<<(unsigned)ctas, cta_threads, smem, st>>>(items, begin, nitems, 0);
+    return cudaGetLastError();
+}
+
 }  // namespace nmfg
 
 #define NMF_HALS_INSTANTIATE_ONE(TV, SV, LV)                                                    \
     template cudaError_t nmfg::hals_launch<TV, SV, LV>(                                         \
         int64_t, int, int64_t, const float *, const float *, int, const float *, float *, int,  \
         const nmfg::HEpilogue &, const nmfg::WEpilogue &, int, cudaStream_t);
-// Both sides.
-// The W side (rows of W, item layout kRow).
-#define NMF_HALS_INSTANTIATE_ROWS(TV, SV) NMF_HALS_INSTANTIATE_ONE(TV, SV, 1)
+// The W side (rows of W, item layout kRow): single and grouped launches.
+#define NMF_HALS_INSTANTIATE_ROWS(TV, SV)                                                   \
+    NMF_HALS_INSTANTIATE_ONE(TV, SV, 1)                                                     \
+    template cudaError_t nmfg::hals_w_launch_grouped<TV, SV>(                               \
+        const nmfg::HalsWItem *, const int64_t *, int, int64_t, int, cudaStream_t);

@@ -11,6 +11,10 @@ cudaError_t hals_launch(int64_t items, int r, int64_t ld, const float *A, const 
                         const float *Xin, float *Xout, int sweeps, const HEpilogue &hep,
                         const WEpilogue &wep, int cta_threads, cudaStream_t st);
 
+template <int T, int S>
+cudaError_t hals_w_launch_grouped(const HalsWItem *items, const int64_t *begin, int nitems,
+                                  int64_t ctas, int cta_threads, cudaStream_t st);
+
 namespace {
 
 // Two lanes per item up to r = 64, four lanes above (r <= 128): every slot
@@ -93,6 +97,50 @@ cudaError_t launch_hals_w(int64_t m, int r, int rs, const float *C, const float 
                           cudaStream_t st) {
     HEpilogue none{};
     return dispatch<1>(m, r, rs, C, D, rs, W_in, W_out, sweeps, none, ep, st);
+}
+
+
+// ------------------------------------------------------------ grouped launches
+// Key: lanes T, slots S and CTA size of the item's single launch, so that a
+// grouped item runs the same CTAs (and sums its error partials in the same
+// order) as its single launch.
+int hals_w_group_key(int64_t m, int r) {
+    const int T = pick_lanes(r);
+    const int need = (r + T - 1) / T < 2 ? 2 : (r + T - 1) / T;
+    const int S = T == 2 ? pick(kSlots2, need) : pick(kSlots4, need);
+    if (S < 0) return -1;
+    return (T * 100 + S) * 8 + cta_threads(m, T) / 32;
+}
+
+void plan_hals_w_item(int64_t m, int r, int rs, const float *C, const float *D,
+                      const float *W_in, float *W_out, int sweeps, const WEpilogue &ep,
+                      HalsWItem *it, int64_t *ctas) {
+    const int64_t nblk = hals_w_num_ctas(m, r);
+    *it = HalsWItem{m, r, rs, C, D, rs, W_in, W_out, sweeps, ep, nblk};
+    *ctas = nblk;
+}
+
+cudaError_t launch_hals_w_grouped(int key, const HalsWItem *items, const int64_t *begin,
+                                  int nitems, int64_t ctas, cudaStream_t st) {
+    const int threads = (key % 8) * 32, TS = key / 8;
+    const int T = TS / 100, S = TS % 100;
+#define NMF_HALS_GROUPED(TV, SV)                                                               \
+    if (T == TV && S == SV)                                                                    \
+        return hals_w_launch_grouped<TV, SV>(items, begin, nitems, ctas, threads, st);
+    NMF_HALS_GROUPED(2, 2) NMF_HALS_GROUPED(2, 3) NMF_HALS_GROUPED(2, 4) NMF_HALS_GROUPED(2, 5)
+    NMF_HALS_GROUPED(2, 6) NMF_HALS_GROUPED(2, 7) NMF_HALS_GROUPED(2, 8) NMF_HALS_GROUPED(2, 9)
+    NMF_HALS_GROUPED(2, 10) NMF_HALS_GROUPED(2, 11) NMF_HALS_GROUPED(2, 12) NMF_HALS_GROUPED(2, 13)
+    NMF_HALS_GROUPED(2, 14) NMF_HALS_GROUPED(2, 15) NMF_HALS_GROUPED(2, 16) NMF_HALS_GROUPED(2, 17)
+    NMF_HALS_GROUPED(2, 18) NMF_HALS_GROUPED(2, 19) NMF_HALS_GROUPED(2, 20) NMF_HALS_GROUPED(2, 21)
+    NMF_HALS_GROUPED(2, 22) NMF_HALS_GROUPED(2, 23) NMF_HALS_GROUPED(2, 24) NMF_HALS_GROUPED(2, 25)
+    NMF_HALS_GROUPED(2, 26) NMF_HALS_GROUPED(2, 27) NMF_HALS_GROUPED(2, 28) NMF_HALS_GROUPED(2, 29)
+    NMF_HALS_GROUPED(2, 30) NMF_HALS_GROUPED(2, 31) NMF_HALS_GROUPED(2, 32)
+    NMF_HALS_GROUPED(4, 17) NMF_HALS_GROUPED(4, 18) NMF_HALS_GROUPED(4, 19) NMF_HALS_GROUPED(4, 20)
+    NMF_HALS_GROUPED(4, 21) NMF_HALS_GROUPED(4, 22) NMF_HALS_GROUPED(4, 23) NMF_HALS_GROUPED(4, 24)
+    NMF_HALS_GROUPED(4, 25) NMF_HALS_GROUPED(4, 26) NMF_HALS_GROUPED(4, 27) NMF_HALS_GROUPED(4, 28)
+    NMF_HALS_GROUPED(4, 29) NMF_HALS_GROUPED(4, 30) NMF_HALS_GROUPED(4, 31) NMF_HALS_GROUPED(4, 32)
+#undef NMF_HALS_GROUPED
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace nmfg

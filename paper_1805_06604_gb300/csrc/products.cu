@@ -49,11 +49,12 @@ __device__ __forceinline__ void kahan_add(float &sum, float &c, float v) {
 // Thread (tx in 0..7, ty in 0..15) owns rows ty + 16a and columns tx + 8b.
 // ---------------------------------------------------------------------------
 template <int TM, int TR>
-__global__ void __launch_bounds__(kThreads)
-xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
-               const float *__restrict__ H, int64_t ldh, float *__restrict__ C,
-               float *__restrict__ C_lo, int rs, int64_t cols_per_split,
-               float *__restrict__ part, unsigned int *__restrict__ tickets) {
+__device__ __forceinline__ void
+xht_body(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
+         const float *__restrict__ H, int64_t ldh, float *__restrict__ C,
+         float *__restrict__ C_lo, int rs, int64_t cols_per_split,
+         float *__restrict__ part, unsigned int *__restrict__ tickets,
+         int64_t tile, int split, int nsplit) {
     constexpr int BM = 16 * TM;
     constexpr int R = 8 * TR;
     extern __shared__ __align__(16) float sm[];
@@ -63,8 +64,7 @@ xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
 
     const int tid = threadIdx.x;
     const int tx = tid % 8, ty = tid / 8;
-    const int64_t row0 = (int64_t)blockIdx.x * BM;
-    const int split = blockIdx.y, nsplit = gridDim.y;
+    const int64_t row0 = tile * BM;
     const int64_t kbeg = (int64_t)split * cols_per_split;
     const int64_t kend = min(ldx, kbeg + cols_per_split);
     const int64_t nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
@@ -173,7 +173,7 @@ xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     }
     // Split-K over the columns of X: partial tiles (hi, lo), summed in split
     // order by the last split of the row tile to finish.
-    float *my = part + ((int64_t)blockIdx.x * nsplit + split) * (2 * BM * R);
+    float *my = part + (tile * nsplit + split) * (2 * BM * R);
 #pragma unroll
     for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -185,7 +185,7 @@ xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     __threadfence();
     __syncthreads();
     if (tid == 0) {
-        const unsigned int tk = atomicAdd(tickets + blockIdx.x, 1u);
+        const unsigned int tk = atomicAdd(tickets + tile, 1u);
         am_last = (tk == (unsigned)nsplit - 1);
     }
     __syncthreads();
@@ -193,7 +193,7 @@ xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     __threadfence();
     // Each thread sums its TM*TR elements over the splits in split order,
     // all of one split's loads in flight at once.
-    const float *base = part + (int64_t)blockIdx.x * nsplit * (2 * BM * R);
+    const float *base = part + tile * nsplit * (2 * BM * R);
     constexpr int J = BM * R / kThreads;
     static_assert(J * kThreads == BM * R, "tile must divide among the threads");
     float fh[J], fl[J];
@@ -225,7 +225,7 @@ xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
             C_lo[row * rs + col] = (fh[j] - c) + fl[j];
         }
     }
-    if (tid == 0) tickets[blockIdx.x] = 0u;
+    if (tid == 0) tickets[tile] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -239,11 +239,11 @@ constexpr int BN = 128;
 constexpr int PADN = BN + 4;
 
 template <int R>
-__global__ void __launch_bounds__(4 * R)
-wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
-               const float *__restrict__ W, float *__restrict__ A, int64_t lda,
-               int64_t rows_per_split, float *__restrict__ part,
-               unsigned int *__restrict__ tickets) {
+__device__ __forceinline__ void
+wtx_body(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
+         const float *__restrict__ W, float *__restrict__ A, int64_t lda,
+         int64_t rows_per_split, float *__restrict__ part,
+         unsigned int *__restrict__ tickets, int64_t tile, int split, int nsplit) {
     constexpr int NT = 4 * R;
     constexpr int PADR = R + 4;
     extern __shared__ __align__(16) float sm[];
@@ -253,8 +253,7 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
 
     const int tid = threadIdx.x;
     const int tx = tid % 16, g = tid / 16;
-    const int64_t col0 = (int64_t)blockIdx.x * BN;
-    const int split = blockIdx.y, nsplit = gridDim.y;
+    const int64_t col0 = tile * BN;
     const int64_t i_begin = (int64_t)split * rows_per_split;
     const int64_t i_end = min(m, i_begin + rows_per_split);
     const int64_t nk = i_end > i_begin ? (i_end - i_begin + BK - 1) / BK : 0;
@@ -343,7 +342,7 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
 
     // Split-K: write this split's partial tile, then the last split of the
     // column tile sums the partials in split order.
-    float *my = part + ((int64_t)blockIdx.x * nsplit + split) * (R * BN);
+    float *my = part + (tile * nsplit + split) * (R * BN);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         float *rowp = my + (4 * g + b) * BN;
@@ -355,7 +354,7 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     __threadfence();
     __syncthreads();
     if (tid == 0) {
-        const unsigned int t = atomicAdd(tickets + blockIdx.x, 1u);
+        const unsigned int t = atomicAdd(tickets + tile, 1u);
         am_last = (t == (unsigned)nsplit - 1);
     }
     __syncthreads();
@@ -363,7 +362,7 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     __threadfence();
     // Each thread sums its float4 words over the splits in split order (Kahan),
     // all of one split's loads in flight at once.
-    const float *base = part + (int64_t)blockIdx.x * nsplit * (R * BN);
+    const float *base = part + tile * nsplit * (R * BN);
     constexpr int J = R * BN / (NT * 4);
     static_assert(J * NT * 4 == R * BN, "tile must divide among the threads");
     float4 fs[J], fc[J];
@@ -395,7 +394,47 @@ wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
                 if (col + q < lda) A[(int64_t)k * lda + col + q] = vv[q];
         }
     }
-    if (tid == 0) tickets[blockIdx.x] = 0u;
+    if (tid == 0) tickets[tile] = 0u;
+}
+
+// Single launches: tile = blockIdx.x, split = blockIdx.y.  Grouped launches:
+// the item's CTAs in tile-major order of its own (tiles x nsplit) grid.
+template <int TM, int TR>
+__global__ void __launch_bounds__(kThreads)
+xht_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
+               const float *__restrict__ H, int64_t ldh, float *__restrict__ C,
+               float *__restrict__ C_lo, int rs, int64_t cols_per_split,
+               float *__restrict__ part, unsigned int *__restrict__ tickets) {
+    xht_body<TM, TR>(X, m, ldx, r, H, ldh, C, C_lo, rs, cols_per_split, part, tickets,
+                     blockIdx.x, blockIdx.y, gridDim.y);
+}
+template <int TM, int TR>
+__global__ void __launch_bounds__(kThreads)
+xht_f32_grouped(const XhtItem *__restrict__ items, const int64_t *__restrict__ begin,
+                int nitems) {
+    int64_t local;
+    const XhtItem &it = items[group_item(begin, nitems, local)];
+    xht_body<TM, TR>(it.X, it.m, it.ldx, it.r, it.H, it.ldh, it.C, it.C_lo, it.rs,
+                     it.cols_per_split, it.part, it.tickets, local % it.tiles,
+                     (int)(local / it.tiles), it.nsplit);
+}
+template <int R>
+__global__ void __launch_bounds__(4 * R)
+wtx_f32_kernel(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
+               const float *__restrict__ W, float *__restrict__ A, int64_t lda,
+               int64_t rows_per_split, float *__restrict__ part,
+               unsigned int *__restrict__ tickets) {
+    wtx_body<R>(X, m, ldx, r, W, A, lda, rows_per_split, part, tickets, blockIdx.x, blockIdx.y,
+                gridDim.y);
+}
+template <int R>
+__global__ void __launch_bounds__(4 * R)
+wtx_f32_grouped(const WtxItem *__restrict__ items, const int64_t *__restrict__ begin,
+                int nitems) {
+    int64_t local;
+    const WtxItem &it = items[group_item(begin, nitems, local)];
+    wtx_body<R>(it.X, it.m, it.ldx, it.r, it.W, it.A, it.lda, it.rows_per_split, it.part,
+                it.tickets, local % it.tiles, (int)(local / it.tiles), it.nsplit);
 }
 
 // Splits of the reduction for a grid of tiles x nsplit CTAs of which
@@ -429,22 +468,70 @@ constexpr int kMaxWtxSplits = 64;
 constexpr int kMaxXhtSplits = 16;
 
 template <int R>
-cudaError_t wtx_launch(const float *X, int64_t m, int64_t ldx, int r, const float *W, float *A,
-                       int64_t lda, float *part, unsigned int *tickets, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)kStages * BK * (PADN + R + 4);
-    auto kern = wtx_f32_kernel<R>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+constexpr size_t wtx_smem() {
+    return sizeof(float) * (size_t)kStages * BK * (PADN + R + 4);
+}
+template <int TM, int TR>
+constexpr size_t xht_smem() {
+    return sizeof(float) * (size_t)kStages * (16 * TM + 8 * TR) * PADK;
+}
+
+// The grid of a product: column (row) tiles x splits of the reduction,
+// chosen from the CTAs the occupancy calculator fits on an SM.
+struct SplitPlan {
+    int64_t tiles;
+    int nsplit;
+    int64_t per_split;      // rows (A) or columns (C) of X per split
+};
+
+template <int R>
+cudaError_t wtx_prepare(SplitPlan *sp, int64_t m, int64_t lda) {
+    const size_t smem = wtx_smem<R>();
+    cudaError_t e = cudaFuncSetAttribute(wtx_f32_kernel<R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(wtx_f32_grouped<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
     if (e != cudaSuccess) return e;
-    static const int per_sm = resident_ctas(kern, 4 * R, smem);
-    const int64_t tiles = (lda + BN - 1) / BN;
+    static const int per_sm = resident_ctas(wtx_f32_kernel<R>, 4 * R, smem);
+    sp->tiles = (lda + BN - 1) / BN;
     int64_t max_split = (m + 8 * BK - 1) / (8 * BK);              // >= 256 rows per split
     if (max_split > kMaxWtxSplits) max_split = kMaxWtxSplits;
-    const int want = balanced_splits(tiles, per_sm, max_split);
-    const int64_t rows_per_split = ((m + want - 1) / want + BK - 1) / BK * BK;
-    const int nsplit = (int)((m + rows_per_split - 1) / rows_per_split);
-    dim3 grid((unsigned)tiles, (unsigned)nsplit);
-    kern<<<grid, 4 * R, smem, st>>>(X, m, ldx, r, W, A, lda, rows_per_split, part, tickets);
+    const int want = balanced_splits(sp->tiles, per_sm, max_split);
+    sp->per_split = ((m + want - 1) / want + BK - 1) / BK * BK;
+    sp->nsplit = (int)((m + sp->per_split - 1) / sp->per_split);
+    return cudaSuccess;
+}
+
+template <int TM, int TR>
+cudaError_t xht_prepare(SplitPlan *sp, int64_t m, int64_t ldx) {
+    constexpr int BM = 16 * TM;
+    const size_t smem = xht_smem<TM, TR>();
+    cudaError_t e = cudaFuncSetAttribute(xht_f32_kernel<TM, TR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(xht_f32_grouped<TM, TR>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    static const int per_sm = resident_ctas(xht_f32_kernel<TM, TR>, kThreads, smem);
+    sp->tiles = (m + BM - 1) / BM;
+    int64_t max_split = (ldx + 8 * BK - 1) / (8 * BK);            // >= 256 columns per split
+    if (max_split > kMaxXhtSplits) max_split = kMaxXhtSplits;
+    const int want = balanced_splits(sp->tiles, per_sm, max_split);
+    sp->per_split = ((ldx + want - 1) / want + BK - 1) / BK * BK;
+    sp->nsplit = (int)((ldx + sp->per_split - 1) / sp->per_split);
+    return cudaSuccess;
+}
+
+template <int R>
+cudaError_t wtx_launch(const float *X, int64_t m, int64_t ldx, int r, const float *W, float *A,
+                       int64_t lda, float *part, unsigned int *tickets, cudaStream_t st) {
+    SplitPlan sp;
+    cudaError_t e = wtx_prepare<R>(&sp, m, lda);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)sp.tiles, (unsigned)sp.nsplit);
+    wtx_f32_kernel<R><<<grid, 4 * R, wtx_smem<R>(), st>>>(X, m, ldx, r, W, A, lda, sp.per_split,
+                                                          part, tickets);
     return cudaGetLastError();
 }
 
@@ -452,22 +539,12 @@ template <int TM, int TR>
 cudaError_t xht_launch(const float *X, int64_t m, int64_t ldx, int r, const float *H,
                        int64_t ldh, float *C, float *C_lo, int rs, float *part,
                        unsigned int *tickets, cudaStream_t st) {
-    constexpr int BM = 16 * TM;
-    constexpr int R = 8 * TR;
-    const size_t smem = sizeof(float) * (size_t)kStages * (BM + R) * PADK;
-    auto kern = xht_f32_kernel<TM, TR>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    SplitPlan sp;
+    cudaError_t e = xht_prepare<TM, TR>(&sp, m, ldx);
     if (e != cudaSuccess) return e;
-    static const int per_sm = resident_ctas(kern, kThreads, smem);
-    const int64_t tiles = (m + BM - 1) / BM;
-    int64_t max_split = (ldx + 8 * BK - 1) / (8 * BK);            // >= 256 columns per split
-    if (max_split > kMaxXhtSplits) max_split = kMaxXhtSplits;
-    const int want = balanced_splits(tiles, per_sm, max_split);
-    const int64_t cols = ((ldx + want - 1) / want + BK - 1) / BK * BK;
-    const int nsplit = (int)((ldx + cols - 1) / cols);
-    dim3 grid((unsigned)tiles, (unsigned)nsplit);
-    kern<<<grid, kThreads, smem, st>>>(X, m, ldx, r, H, ldh, C, C_lo, rs, cols, part, tickets);
+    dim3 grid((unsigned)sp.tiles, (unsigned)sp.nsplit);
+    xht_f32_kernel<TM, TR><<<grid, kThreads, xht_smem<TM, TR>(), st>>>(
+        X, m, ldx, r, H, ldh, C, C_lo, rs, sp.per_split, part, tickets);
     return cudaGetLastError();
 }
 
@@ -527,6 +604,102 @@ cudaError_t launch_xht_f32(const float *X, int64_t m, int64_t ldx, int r, const 
         NMF_XHT_CASE(9) NMF_XHT_CASE(10) NMF_XHT_CASE(11) NMF_XHT_CASE(12)
         NMF_XHT_CASE(13) NMF_XHT_CASE(14) NMF_XHT_CASE(15) NMF_XHT_CASE(16)
 #undef NMF_XHT_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+
+// ------------------------------------------------------------ grouped launches
+// Key of a product variant: A = W^T X by rs; C = X H^T by (tile height, rs / 8).
+int wtx_group_key(int rs) { return rs; }
+int xht_group_key(int64_t m, int r) { return (xht_big(m, r) ? 4 : 2) * 32 + (r + 7) / 8; }
+
+cudaError_t plan_wtx_item(const float *X, int64_t m, int64_t lda, int64_t ldx, int r,
+                          const float *W, int rs, float *A, void *ws, unsigned int *tickets,
+                          WtxItem *it, int64_t *ctas) {
+    SplitPlan sp{};
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (rs) {
+#define NMF_WTX_PLAN(RV)                            \
+    case RV:                                        \
+        e = wtx_prepare<RV>(&sp, m, lda);           \
+        break;
+        NMF_WTX_PLAN(8) NMF_WTX_PLAN(16) NMF_WTX_PLAN(24) NMF_WTX_PLAN(32)
+        NMF_WTX_PLAN(40) NMF_WTX_PLAN(48) NMF_WTX_PLAN(56) NMF_WTX_PLAN(64)
+        NMF_WTX_PLAN(72) NMF_WTX_PLAN(80) NMF_WTX_PLAN(88) NMF_WTX_PLAN(96)
+        NMF_WTX_PLAN(104) NMF_WTX_PLAN(112) NMF_WTX_PLAN(120) NMF_WTX_PLAN(128)
+#undef NMF_WTX_PLAN
+        default: break;
+    }
+    if (e != cudaSuccess) return e;
+    *it = WtxItem{X, m, ldx, r, W, A, lda, sp.per_split, static_cast<float *>(ws), tickets,
+                  sp.tiles, sp.nsplit};
+    *ctas = sp.tiles * sp.nsplit;
+    return cudaSuccess;
+}
+
+cudaError_t launch_wtx_grouped(int key, const WtxItem *items, const int64_t *begin, int nitems,
+                               int64_t ctas, cudaStream_t st) {
+    if (nitems < 1 || ctas < 1) return cudaSuccess;
+    switch (key) {
+#define NMF_WTX_GROUPED(RV)                                                                  \
+    case RV:                                                                                 \
+        wtx_f32_grouped<RV><<<(unsigned)ctas, 4 * RV, wtx_smem<RV>(), st>>>(items, begin,     \
+                                                                           nitems);           \
+        return cudaGetLastError();
+        NMF_WTX_GROUPED(8) NMF_WTX_GROUPED(16) NMF_WTX_GROUPED(24) NMF_WTX_GROUPED(32)
+        NMF_WTX_GROUPED(40) NMF_WTX_GROUPED(48) NMF_WTX_GROUPED(56) NMF_WTX_GROUPED(64)
+        NMF_WTX_GROUPED(72) NMF_WTX_GROUPED(80) NMF_WTX_GROUPED(88) NMF_WTX_GROUPED(96)
+        NMF_WTX_GROUPED(104) NMF_WTX_GROUPED(112) NMF_WTX_GROUPED(120) NMF_WTX_GROUPED(128)
+#undef NMF_WTX_GROUPED
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t plan_xht_item(const float *X, int64_t m, int64_t ldx, int r, const float *H,
+                          int64_t ldh, float *C, float *C_lo, int rs, void *ws,
+                          unsigned int *tickets, XhtItem *it, int64_t *ctas) {
+    const bool big = xht_big(m, r);
+    SplitPlan sp{};
+    cudaError_t e = cudaErrorInvalidValue;
+    switch ((r + 7) / 8) {
+#define NMF_XHT_PLAN(TRV)                                                                    \
+    case TRV:                                                                                \
+        e = big ? xht_prepare<4, TRV>(&sp, m, ldx) : xht_prepare<2, TRV>(&sp, m, ldx);       \
+        break;
+        NMF_XHT_PLAN(1) NMF_XHT_PLAN(2) NMF_XHT_PLAN(3) NMF_XHT_PLAN(4)
+        NMF_XHT_PLAN(5) NMF_XHT_PLAN(6) NMF_XHT_PLAN(7) NMF_XHT_PLAN(8)
+        NMF_XHT_PLAN(9) NMF_XHT_PLAN(10) NMF_XHT_PLAN(11) NMF_XHT_PLAN(12)
+        NMF_XHT_PLAN(13) NMF_XHT_PLAN(14) NMF_XHT_PLAN(15) NMF_XHT_PLAN(16)
+#undef NMF_XHT_PLAN
+        default: break;
+    }
+    if (e != cudaSuccess) return e;
+    *it = XhtItem{X, m, ldx, r, H, ldh, C, C_lo, rs, sp.per_split, static_cast<float *>(ws),
+                  tickets, sp.tiles, sp.nsplit};
+    *ctas = sp.tiles * sp.nsplit;
+    return cudaSuccess;
+}
+
+cudaError_t launch_xht_grouped(int key, const XhtItem *items, const int64_t *begin, int nitems,
+                               int64_t ctas, cudaStream_t st) {
+    if (nitems < 1 || ctas < 1) return cudaSuccess;
+    const int tm = key / 32, tr = key % 32;
+    switch (tr) {
+#define NMF_XHT_GROUPED(TRV)                                                                 \
+    case TRV:                                                                                \
+        if (tm == 4)                                                                         \
+            xht_f32_grouped<4, TRV><<<(unsigned)ctas, kThreads, xht_smem<4, TRV>(), st>>>(    \
+                items, begin, nitems);                                                       \
+        else                                                                                 \
+            xht_f32_grouped<2, TRV><<<(unsigned)ctas, kThreads, xht_smem<2, TRV>(), st>>>(    \
+                items, begin, nitems);                                                       \
+        return cudaGetLastError();
+        NMF_XHT_GROUPED(1) NMF_XHT_GROUPED(2) NMF_XHT_GROUPED(3) NMF_XHT_GROUPED(4)
+        NMF_XHT_GROUPED(5) NMF_XHT_GROUPED(6) NMF_XHT_GROUPED(7) NMF_XHT_GROUPED(8)
+        NMF_XHT_GROUPED(9) NMF_XHT_GROUPED(10) NMF_XHT_GROUPED(11) NMF_XHT_GROUPED(12)
+        NMF_XHT_GROUPED(13) NMF_XHT_GROUPED(14) NMF_XHT_GROUPED(15) NMF_XHT_GROUPED(16)
+#undef NMF_XHT_GROUPED
         default: return cudaErrorInvalidValue;
     }
 }

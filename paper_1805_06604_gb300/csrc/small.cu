@@ -96,13 +96,13 @@ constexpr int GBK = 32;
 // is kept as an unevaluated pair hi + lo (the Gram of H_y also feeds the
 // Remark 1 error, whose cancellation needs it to about 2^-40 relative).
 template <int RB, bool ROWS, bool EXACT>
-__global__ void __launch_bounds__(256)
-gram_partial_kernel(const float *__restrict__ M, int64_t N, int64_t ldm, int r,
-                    int64_t chunk, float *__restrict__ part, float *__restrict__ part_lo, int rs) {
+__device__ __forceinline__ void
+gram_partial_body(const float *__restrict__ M, int64_t N, int64_t ldm, int r, int64_t chunk,
+                  float *__restrict__ part, float *__restrict__ part_lo, int rs, int64_t bid) {
     constexpr int R = 16 * RB;
     __shared__ float Ms[GBK][R + 1];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int64_t i0 = (int64_t)blockIdx.x * chunk;
+    const int64_t i0 = bid * chunk;
     const int64_t i1 = min(N, i0 + chunk);
     float acc[RB][RB], comp[RB][RB];
 #pragma unroll
@@ -170,7 +170,7 @@ gram_partial_kernel(const float *__restrict__ M, int64_t N, int64_t ldm, int r,
         }
         __syncthreads();
     }
-    float *out = part + (int64_t)blockIdx.x * rs * rs;
+    float *out = part + bid * rs * rs;
 #pragma unroll
     for (int a = 0; a < RB; ++a)
 #pragma unroll
@@ -179,12 +179,28 @@ gram_partial_kernel(const float *__restrict__ M, int64_t N, int64_t ldm, int r,
             if (i < rs && j < rs) {
                 if constexpr (EXACT) {
                     out[i * rs + j] = acc[a][b];
-                    part_lo[(int64_t)blockIdx.x * rs * rs + i * rs + j] = comp[a][b];
+                    part_lo[bid * rs * rs + i * rs + j] = comp[a][b];
                 } else {
                     out[i * rs + j] = acc[a][b] - comp[a][b];
                 }
             }
         }
+}
+
+template <int RB, bool ROWS, bool EXACT>
+__global__ void __launch_bounds__(256)
+gram_partial_kernel(const float *__restrict__ M, int64_t N, int64_t ldm, int r,
+                    int64_t chunk, float *__restrict__ part, float *__restrict__ part_lo, int rs) {
+    gram_partial_body<RB, ROWS, EXACT>(M, N, ldm, r, chunk, part, part_lo, rs, blockIdx.x);
+}
+template <int RB, bool ROWS, bool EXACT>
+__global__ void __launch_bounds__(256)
+gram_partial_grouped(const GramItem *__restrict__ items, const int64_t *__restrict__ begin,
+                     int nitems) {
+    int64_t local;
+    const GramItem &it = items[group_item(begin, nitems, local)];
+    gram_partial_body<RB, ROWS, EXACT>(it.M, it.N, it.ldm, it.r, it.chunk, it.part, it.part_lo,
+                                       it.rs, local);
 }
 
 // Sum of the per-chunk partial Grams.  A CTA owns 32 consecutive entries
@@ -193,11 +209,11 @@ gram_partial_kernel(const float *__restrict__ M, int64_t N, int64_t ldm, int r,
 // and the eight warp sums are combined in warp order (deterministic).
 constexpr int kRedWarps = 8;
 
-__global__ void __launch_bounds__(kRedWarps * 32)
-gram_reduce_kernel(const float *__restrict__ part, int nparts, int rs, float *__restrict__ G) {
+__device__ __forceinline__ void gram_reduce_body(const float *__restrict__ part, int nparts,
+                                                 int rs, float *__restrict__ G, int bid) {
     __shared__ float sh[kRedWarps][32], sc[kRedWarps][32];
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-    const int e = blockIdx.x * 32 + lane;
+    const int e = bid * 32 + lane;
     const int ne = rs * rs;
     float s = 0.0f, c = 0.0f;
     if (e < ne) {
@@ -219,12 +235,14 @@ gram_reduce_kernel(const float *__restrict__ part, int nparts, int rs, float *__
 
 // Pairs (hi_p, lo_p) summed exactly into G + G_lo (hi part rounded to FP32),
 // with the same decomposition.
-__global__ void __launch_bounds__(kRedWarps * 32)
-gram_reduce_exact_kernel(const float *__restrict__ part, const float *__restrict__ part_lo,
-                         int nparts, int rs, float *__restrict__ G, float *__restrict__ G_lo) {
+__device__ __forceinline__ void gram_reduce_exact_body(const float *__restrict__ part,
+                                                       const float *__restrict__ part_lo,
+                                                       int nparts, int rs,
+                                                       float *__restrict__ G,
+                                                       float *__restrict__ G_lo, int bid) {
     __shared__ float sh[kRedWarps][32], sl[kRedWarps][32];
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-    const int e = blockIdx.x * 32 + lane;
+    const int e = bid * 32 + lane;
     const int ne = rs * rs;
     float hi = 0.0f, lo = 0.0f;
     if (e < ne) {
@@ -252,6 +270,27 @@ gram_reduce_exact_kernel(const float *__restrict__ part, const float *__restrict
         G[e] = g;
         G_lo[e] = ge;
     }
+}
+
+__global__ void __launch_bounds__(kRedWarps * 32)
+gram_reduce_kernel(const float *__restrict__ part, int nparts, int rs, float *__restrict__ G) {
+    gram_reduce_body(part, nparts, rs, G, blockIdx.x);
+}
+__global__ void __launch_bounds__(kRedWarps * 32)
+gram_reduce_exact_kernel(const float *__restrict__ part, const float *__restrict__ part_lo,
+                         int nparts, int rs, float *__restrict__ G, float *__restrict__ G_lo) {
+    gram_reduce_exact_body(part, part_lo, nparts, rs, G, G_lo, blockIdx.x);
+}
+template <bool EXACT>
+__global__ void __launch_bounds__(kRedWarps * 32)
+gram_reduce_grouped(const GramItem *__restrict__ items, const int64_t *__restrict__ begin,
+                    int nitems) {
+    int64_t local;
+    const GramItem &it = items[group_item(begin, nitems, local)];
+    if constexpr (EXACT)
+        gram_reduce_exact_body(it.part, it.part_lo, it.nparts, it.rs, it.G, it.G_lo, (int)local);
+    else
+        gram_reduce_body(it.part, it.nparts, it.rs, it.G, (int)local);
 }
 
 struct GramPlan {
@@ -384,15 +423,15 @@ __global__ void init_state_kernel(const ErrPartial *__restrict__ part, int npart
 // ---------------------------------------------------------------- finalize
 // W part: q < m*rs, H part: q < r*ldh.  Padded entries are zero everywhere
 // and stay zero.
-__global__ void __launch_bounds__(256)
-finalize_kernel(int64_t nw, int64_t nh, float *__restrict__ W, float *__restrict__ H,
-                float *__restrict__ Wy, float *__restrict__ Hy, const float *__restrict__ Wn,
-                const float *__restrict__ Hn, const float *__restrict__ Hw,
-                const DevState *__restrict__ state, DevParams p) {
+__device__ __forceinline__ void
+finalize_body(int64_t nw, int64_t nh, float *__restrict__ W, float *__restrict__ H,
+              float *__restrict__ Wy, float *__restrict__ Hy, const float *__restrict__ Wn,
+              const float *__restrict__ Hn, const float *__restrict__ Hw,
+              const DevState *__restrict__ state, const DevParams &p, int64_t bid, int64_t nblk) {
     const int acc = state->accepted;
     const float beta = (float)state->beta_used;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nw + nh; q += stride) {
+    const int64_t stride = nblk * blockDim.x;
+    for (int64_t q = bid * blockDim.x + threadIdx.x; q < nw + nh; q += stride) {
         if (q < nw) {
             if (acc) {
                 const float wold = W[q], wn = Wn[q];
@@ -417,6 +456,23 @@ finalize_kernel(int64_t nw, int64_t nh, float *__restrict__ W, float *__restrict
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(256)
+finalize_kernel(int64_t nw, int64_t nh, float *__restrict__ W, float *__restrict__ H,
+                float *__restrict__ Wy, float *__restrict__ Hy, const float *__restrict__ Wn,
+                const float *__restrict__ Hn, const float *__restrict__ Hw,
+                const DevState *__restrict__ state, DevParams p) {
+    finalize_body(nw, nh, W, H, Wy, Hy, Wn, Hn, Hw, state, p, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(256)
+finalize_grouped(const FinalizeItem *__restrict__ items, const int64_t *__restrict__ begin,
+                 int nitems) {
+    int64_t local;
+    const int i = group_item(begin, nitems, local);
+    const FinalizeItem &it = items[i];
+    finalize_body(it.nw, it.nh, it.W, it.H, it.Wy, it.Hy, it.Wn, it.Hn, it.Hw, it.state, it.p,
+                  local, __ldg(begin + i + 1) - __ldg(begin + i));
 }
 
 __global__ void nonfinite_kernel(const float *__restrict__ v, int64_t count, int *flag) {
@@ -513,6 +569,76 @@ cudaError_t launch_nonfinite_scan(const float *v, int64_t count, int *flag, cuda
     if (blocks > 4 * kNumSMs) blocks = 4 * kNumSMs;
     if (blocks < 1) blocks = 1;
     nonfinite_kernel<<<(unsigned)blocks, 256, 0, st>>>(v, count, flag);
+    return cudaGetLastError();
+}
+
+
+// ------------------------------------------------------------ grouped launches
+// (The Gram of W in FP32 and the error-free Gram of H: the variants of the
+// batched HALS iteration.)
+int gram_group_key(int r, bool rows, bool exact) {
+    return ((r + 15) / 16) * 4 + (rows ? 2 : 0) + (exact ? 1 : 0);
+}
+
+void plan_gram_item(const float *M, int64_t N, int64_t ldm, int r, int rs, float *G,
+                    float *G_lo, void *ws, GramItem *it, int64_t *ctas_partial,
+                    int64_t *ctas_reduce) {
+    const GramPlan p = plan_gram(N);
+    float *part = static_cast<float *>(ws);
+    *it = GramItem{M, N, ldm, r, rs, p.chunk, part, part + (size_t)p.nparts * rs * rs, p.nparts,
+                   G, G_lo};
+    *ctas_partial = p.nparts;
+    *ctas_reduce = (rs * rs + 31) / 32;
+}
+
+cudaError_t launch_gram_partial_grouped(int key, const GramItem *items, const int64_t *begin,
+                                        int nitems, int64_t ctas, cudaStream_t st) {
+    if (nitems < 1 || ctas < 1) return cudaSuccess;
+    const int rb = key / 4;
+    const bool rows = (key & 2) != 0, exact = (key & 1) != 0;
+    switch (rb) {
+#define NMF_GRAM_GROUPED(RBV)                                                                  \
+    case RBV:                                                                                  \
+        if (rows && !exact)                                                                    \
+            gram_partial_grouped<RBV, true, false><<<(unsigned)ctas, 256, 0, st>>>(items, begin, \
+                                                                                  nitems);     \
+        else if (!rows && exact)                                                               \
+            gram_partial_grouped<RBV, false, true><<<(unsigned)ctas, 256, 0, st>>>(items, begin, \
+                                                                                  nitems);     \
+        else                                                                                   \
+            return cudaErrorInvalidValue;                                                      \
+        return cudaGetLastError();
+        NMF_GRAM_GROUPED(1) NMF_GRAM_GROUPED(2) NMF_GRAM_GROUPED(3) NMF_GRAM_GROUPED(4)
+        NMF_GRAM_GROUPED(5) NMF_GRAM_GROUPED(6) NMF_GRAM_GROUPED(7) NMF_GRAM_GROUPED(8)
+#undef NMF_GRAM_GROUPED
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_gram_reduce_grouped(bool exact, const GramItem *items, const int64_t *begin,
+                                       int nitems, int64_t ctas, cudaStream_t st) {
+    if (nitems < 1 || ctas < 1) return cudaSuccess;
+    if (exact)
+        gram_reduce_grouped<true><<<(unsigned)ctas, kRedWarps * 32, 0, st>>>(items, begin, nitems);
+    else
+        gram_reduce_grouped<false><<<(unsigned)ctas, kRedWarps * 32, 0, st>>>(items, begin, nitems);
+    return cudaGetLastError();
+}
+
+void plan_finalize_item(int64_t m, int rs, int r, int64_t ldh, float *W, float *H, float *Wy,
+                        float *Hy, const float *Wn, const float *Hn, const float *Hw,
+                        const DevState *state, DevParams p, FinalizeItem *it, int64_t *ctas) {
+    const int64_t nw = m * rs, nh = (int64_t)r * ldh;
+    int64_t blocks = (nw + nh + 255) / 256;
+    if (blocks > 8 * kNumSMs) blocks = 8 * kNumSMs;
+    *it = FinalizeItem{nw, nh, W, H, Wy, Hy, Wn, Hn, Hw, state, p};
+    *ctas = blocks;
+}
+
+cudaError_t launch_finalize_grouped(const FinalizeItem *items, const int64_t *begin, int nitems,
+                                    int64_t ctas, cudaStream_t st) {
+    if (nitems < 1 || ctas < 1) return cudaSuccess;
+    finalize_grouped<<<(unsigned)ctas, 256, 0, st>>>(items, begin, nitems);
     return cudaGetLastError();
 }
 

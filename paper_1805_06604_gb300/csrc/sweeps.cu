@@ -109,12 +109,12 @@ __device__ __forceinline__ void st_vec(float *p, const float (&v)[B]) {
 }
 
 template <int LAYOUT, int B>
-__global__ void __launch_bounds__(kThreads)
-sweep_kernel(int64_t items, int r, int64_t ld, int nt,
-             const float *__restrict__ Aglob,     // right-hand side a (A or C)
-             const float *__restrict__ Gglob,     // Gram (G or D), rs x rs
-             int rs, const float *Xin, float *Xout, int sweeps,   // may alias (one sweep in place)
-             HEpilogue hep) {
+__device__ __forceinline__ void
+sweep_body(int64_t items, int r, int64_t ld, int nt,
+           const float *__restrict__ Aglob,     // right-hand side a (A or C)
+           const float *__restrict__ Gglob,     // Gram (G or D), rs x rs
+           int rs, const float *Xin, float *Xout, int sweeps,   // may alias (one sweep in place)
+           const HEpilogue &hep, int64_t bid) {
     // A programmatically dependent successor (the tensor-core X product)
     // may start streaming X now; it waits for this grid before reading H_y.
     asm volatile("griddepcontrol.launch_dependents;");
@@ -123,11 +123,11 @@ sweep_kernel(int64_t items, int r, int64_t ld, int nt,
     const int rp = L.rp, rps = L.rps, nb = rp / B;
     float *Gs = smem + L.g, *xs = smem + L.x, *as = smem + L.a, *Pb = smem + L.p;
     float *inv = smem + L.inv;
-    const int64_t item0 = (int64_t)blockIdx.x * nt;
+    const int64_t item0 = bid * nt;
     const int nhere = (int)(items - item0 < (int64_t)nt ? items - item0 : (int64_t)nt);
     const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
     __shared__ double sh32[32];
-    if (sweep_stopped(hep.stop, sh32)) return;         // A-HALS early stop (delta rule)
+    if (sweep_stopped(hep.stop, sh32, bid)) return;    // A-HALS early stop (delta rule)
 
     for (int e = tid; e < rp * rp; e += kThreads) {
         const int k = e / rp, i = e % rp;
@@ -303,8 +303,25 @@ sweep_kernel(int64_t items, int r, int64_t ld, int nt,
             }
         }
     }
-    sweep_record(hep.stop, moved, sh32);
+    sweep_record(hep.stop, moved, sh32, bid);
 
+}
+
+template <int LAYOUT, int B>
+__global__ void __launch_bounds__(kThreads)
+sweep_kernel(int64_t items, int r, int64_t ld, int nt, const float *__restrict__ Aglob,
+             const float *__restrict__ Gglob, int rs, const float *Xin, float *Xout, int sweeps,
+             HEpilogue hep) {
+    sweep_body<LAYOUT, B>(items, r, ld, nt, Aglob, Gglob, rs, Xin, Xout, sweeps, hep, blockIdx.x);
+}
+template <int LAYOUT, int B>
+__global__ void __launch_bounds__(kThreads)
+sweep_grouped(const SweepItem *__restrict__ table, const int64_t *__restrict__ begin,
+              int nitems) {
+    int64_t local;
+    const SweepItem &it = table[group_item(begin, nitems, local)];
+    sweep_body<LAYOUT, B>(it.items, it.r, it.ld, it.nt, it.A, it.G, it.rs, it.Xin, it.Xout,
+                          it.sweeps, it.hep, local);
 }
 
 // Coordinates per block.  Each block costs one hand-over between the
@@ -353,6 +370,32 @@ cudaError_t launch_hals_h(int64_t n, int64_t ldh, int r, int rs, const float *A,
                           const float *G, const float *H_in, float *H_out, int sweeps,
                           const HEpilogue &ep, cudaStream_t st) {
     return sweep_launch<kColumn, kBlockH>(n, r, ldh, A, G, rs, H_in, H_out, sweeps, ep, st);
+}
+
+
+// ------------------------------------------------------------ grouped launches
+// The H sweeps of many problems in one launch.  The columns per CTA (nt <=
+// 32; 0: the single launch's choice) set only how the columns are grouped
+// into CTAs: every column's updates are the same whatever the grouping.
+void plan_sweep_h_item(int64_t n, int64_t ldh, int r, int rs, const float *A, const float *G,
+                       const float *H_in, float *H_out, int sweeps, const HEpilogue &ep, int nt,
+                       SweepItem *it, int64_t *ctas) {
+    if (nt <= 0 || nt > kItems) nt = items_per_cta(n);
+    *it = SweepItem{n, r, ldh, nt, A, G, rs, H_in, H_out, sweeps, ep};
+    *ctas = (n + nt - 1) / nt;
+}
+
+cudaError_t launch_sweep_h_grouped(const SweepItem *items, const int64_t *begin, int nitems,
+                                   int64_t ctas, int max_r, cudaStream_t st) {
+    if (nitems < 1 || ctas < 1) return cudaSuccess;
+    const Layout L(max_r, kBlockH);
+    const size_t smem = sizeof(float) * (size_t)L.total;
+    auto kern = sweep_grouped<kColumn, kBlockH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)ctas, kThreads, smem, st>>>(items, begin, nitems);
+    return cudaGetLastError();
 }
 
 }  // namespace nmfg

@@ -63,6 +63,12 @@ class nmf_scalars(ct.Structure):
                 ("e_last", ct.c_double), ("e_prev", ct.c_double), ("k", ct.c_int64)]
 
 
+class nmf_batch_plan(ct.Structure):
+    _fields_ = [("grouped", ct.c_int32), ("branches", ct.c_int32),
+                ("h_cols_per_cta", ct.c_int32), ("launches_per_iter", ct.c_int32),
+                ("ms_per_iter", ct.c_double)]
+
+
 _lib = None
 _SIGS = {
     "nmf_params_default": [ct.POINTER(nmf_params)],
@@ -103,6 +109,8 @@ _SIGS = {
     "nmf_batch_get_info": [ct.c_void_p, ct.c_int32, ct.POINTER(nmf_info)],
     "nmf_batch_get_factors": [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_int32],
     "nmf_batch_schedule": [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_double)],
+    "nmf_batch_get_plan": [ct.c_void_p, ct.POINTER(nmf_batch_plan)],
+    "nmf_batch_set_plan": [ct.c_void_p, ct.POINTER(nmf_batch_plan)],
     "nmf_batch_destroy": [ct.c_void_p],
 }
 PHASES = ["gram_w", "wtx", "hals_h", "gram_h", "xht", "hals_w", "finalize"]
@@ -434,6 +442,15 @@ class Batch:
         b, ms = ct.c_int32(), ct.c_double()
         _check(load().nmf_batch_schedule(self.h, ct.byref(b), ct.byref(ms)), "nmf_batch_schedule")
         return b.value, ms.value
+
+    def plan(self) -> nmf_batch_plan:
+        out = nmf_batch_plan()
+        _check(load().nmf_batch_get_plan(self.h, ct.byref(out)), "nmf_batch_get_plan")
+        return out
+
+    def set_plan(self, grouped, branches, h_cols_per_cta=0):
+        pl = nmf_batch_plan(int(grouped), int(branches), int(h_cols_per_cta), 0, 0.0)
+        _check(load().nmf_batch_set_plan(self.h, ct.byref(pl)), "nmf_batch_set_plan")
 
     def close(self):
         if self.h is not None and self.h.value:

@@ -83,9 +83,25 @@ def batch_main(args):
         e1.record()
         torch.cuda.synchronize()
         res[name] = e0.elapsed_time(e1) / K
+    pl = b.plan()
+    chosen = {"grouped": pl.grouped, "branches": pl.branches, "h_cols": pl.h_cols_per_cta,
+              "launches_per_iter": pl.launches_per_iter}
+    # Every schedule the tuner considers, timed the same way.
+    plans = {}
+    for g, br, cols in ((0, 64, 0), (0, 16, 0), (1, 1, 32), (1, 16, 32), (1, 1, 16),
+                        (1, 16, 16), (1, 16, 8)):
+        b.set_plan(g, br, cols)
+        b.step(1)
+        torch.cuda.synchronize()
+        e0.record()
+        b.step(K)
+        e1.record()
+        torch.cuda.synchronize()
+        plans[f"{'grouped' if g else 'chains'}_b{br}_c{cols}"] = round(e0.elapsed_time(e1) / K, 3)
     flops = sum(4.0 * P.m * P.n * P.r for P in probs)
     b.close()
     print(json.dumps({"instances": args.batch, "sum_mn": int(sum(P.m * P.n for P in probs)),
+                      "plan": chosen, "plans_ms_per_iter": plans,
                       "branches": branches, "autotune_ms_per_iter": round(tuned, 3),
                       "create_s": round(t_create, 2), "iters": K,
                       "graph_ms_per_iter": round(res["graph"], 3),

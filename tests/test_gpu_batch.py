@@ -1,9 +1,11 @@
 """Batched solver: many uneven instances in one CUDA graph per iteration.
 
-Every instance runs the same kernels in the same order as a single-instance
-solver, only scheduled concurrently, so results are compared bit for bit
-with nmf_create/nmf_step (which the parity tests check against the oracle),
-and the per-instance launch loop must give identical results too."""
+Every instance runs the same kernels, with the same tiles, splits and CTAs,
+as a single-instance solver -- grouped into one launch per phase and kernel
+variant, or as per-instance chains on concurrent branches -- so results are
+compared bit for bit with nmf_create/nmf_step (which the parity tests check
+against the oracle), and the per-instance launch loop must give identical
+results too."""
 import numpy as np
 import pytest
 
@@ -129,3 +131,82 @@ def test_per_instance_parameters_are_validated():
     h = ct.c_void_p()
     st = nmf.load().nmf_batch_create_params(ct.byref(h), 1, None, None, None, None, 0, None, None)
     assert st == nmf.NMF_EINVAL
+
+
+def _mixed_problems():
+    """Instances of every variant class the grouped launches key on: r from
+    1 to 40 (one to five 8-wide column groups, lane slot counts 2..20), a
+    tall instance whose products split their reduction, ragged m and n."""
+    out = _problems(14, seed=11, mn=(40, 600))
+    out.append(wl.low_rank(3100, 260, 40, seed=12, noise=0.01))
+    out.append(wl.low_rank(300, 2900, 13, seed=13, noise=0.01))
+    out.append(wl.low_rank(90, 70, 1, seed=14, noise=0.01))
+    return out
+
+
+@pytest.mark.parametrize("grouped,branches,cols", [(1, 1, 32), (1, 16, 16), (1, 4, 7),
+                                                   (0, 4, 0)])
+def test_every_plan_matches_single_solvers(grouped, branches, cols):
+    """Grouped launches (one per phase and kernel variant over all instances)
+    and per-instance chains: each instance bit-identical to its single
+    solver after K iterations, whatever the schedule."""
+    probs = _mixed_problems()
+    K = 9
+    with nmf.Batch([(P.X, P.r, P.W0, P.H0) for P in probs]) as b:
+        b.set_plan(grouped, branches, cols)
+        pl = b.plan()
+        assert pl.grouped == grouped and pl.branches == branches
+        if grouped:
+            assert pl.launches_per_iter < 9 * len(probs) // 2, pl.launches_per_iter
+        else:
+            assert pl.launches_per_iter == 9 * len(probs)
+        b.step(K)
+        for i, P in enumerate(probs):
+            W, H = b.factors(i)
+            with nmf.Solver(P.X, P.r, P.W0, P.H0) as s:
+                s.step(K)
+                Ws, Hs = s.factors()
+                np.testing.assert_array_equal(W, Ws, err_msg=f"instance {i}")
+                np.testing.assert_array_equal(H, Hs, err_msg=f"instance {i}")
+                bi, si = b.info(i), s.info()
+                assert bi.e_last == si.e_last and bi.beta == si.beta and bi.k == K
+                assert bi.device_status == 0
+
+
+def test_grouped_plan_with_per_instance_parameters():
+    """The parameter-study form (same X, hp and the beta schedule varying per
+    instance) under grouped launches equals single solvers bit for bit."""
+    from paper_1805_06604_gb300 import sweep
+    P = wl.low_rank(150, 110, 9, seed=15)
+    vs = sweep.variants(hp=(1, 2, 3), beta0=(0.25, 0.75), eta=(1.5,), gammas=((1.05, 1.01),))
+    K = 12
+    with nmf.Batch([(P.X, P.r, P.W0, P.H0)] * len(vs), per_instance=[ov for _, _, ov in vs]) as b:
+        b.set_plan(1, 8, 0)
+        b.step(K)
+        for i, (_, _, ov) in enumerate(vs):
+            W, H = b.factors(i)
+            with nmf.Solver(P.X, P.r, P.W0, P.H0, **ov) as s:
+                s.step(K)
+                Ws, Hs = s.factors()
+                np.testing.assert_array_equal(W, Ws)
+                np.testing.assert_array_equal(H, Hs)
+
+
+def test_plan_is_validated():
+    """Out-of-range fields give NMF_EINVAL; grouped launches for a batch with
+    a tensor-core instance give NMF_ENOTSUP, and the batch keeps working with
+    its tuned schedule."""
+    probs = _problems(3, seed=16)
+    with nmf.Batch([(P.X, P.r, P.W0, P.H0) for P in probs],
+                   per_instance=[{}, {"precision": nmf.NMF_PREC_TF32}, {}]) as b:
+        before = b.plan()
+        assert before.grouped == 0
+        for bad in [(2, 1, 0), (1, 0, 0), (0, 65, 0), (1, 1, 33), (1, 1, -1)]:
+            with pytest.raises(nmf.NmfError) as ei:
+                b.set_plan(*bad)
+            assert ei.value.status == nmf.NMF_EINVAL
+        with pytest.raises(nmf.NmfError) as ei:
+            b.set_plan(1, 1, 0)
+        assert ei.value.status == nmf.NMF_ENOTSUP
+        b.step(3)
+        assert all(b.info(i).k == 3 and b.info(i).device_status == 0 for i in range(3))
