@@ -302,17 +302,27 @@ wtx_body(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int c = 0; c < 8; ++c) blk[b][c] = 0.0f;
+        // Paired FP32 FMAs: columns (c, c + 1) of a row of A in one
+        // instruction, each the same IEEE FMA as a scalar one.
 #pragma unroll 4
         for (int ii = 0; ii < BK; ++ii) {
             const float4 w = *reinterpret_cast<const float4 *>(ws + ii * PADR + 4 * g);
             const float4 x0 = *reinterpret_cast<const float4 *>(xs + ii * PADN + 4 * tx);
             const float4 x1 = *reinterpret_cast<const float4 *>(xs + ii * PADN + 64 + 4 * tx);
             const float wv[4] = {w.x, w.y, w.z, w.w};
-            const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            const float2 xv[4] = {make_float2(x0.x, x0.y), make_float2(x0.z, x0.w),
+                                  make_float2(x1.x, x1.y), make_float2(x1.z, x1.w)};
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
+            for (int b = 0; b < 4; ++b) {
+                const float2 wb = make_float2(wv[b], wv[b]);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) blk[b][c] = fmaf(wv[b], xv[c], blk[b][c]);
+                for (int c = 0; c < 4; ++c) {
+                    const float2 t = __ffma2_rn(wb, xv[c],
+                                                make_float2(blk[b][2 * c], blk[b][2 * c + 1]));
+                    blk[b][2 * c] = t.x;
+                    blk[b][2 * c + 1] = t.y;
+                }
+            }
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b)

@@ -628,8 +628,10 @@ cudaError_t launch_gram_reduce_grouped(bool exact, const GramItem *items, const 
 void plan_finalize_item(int64_t m, int rs, int r, int64_t ldh, float *W, float *H, float *Wy,
                         float *Hy, const float *Wn, const float *Hn, const float *Hw,
                         const DevState *state, DevParams p, FinalizeItem *it, int64_t *ctas) {
+    // Elementwise, so any grid gives the same result: eight entries per
+    // thread (the many small instances of a batch need no more CTAs).
     const int64_t nw = m * rs, nh = (int64_t)r * ldh;
-    int64_t blocks = (nw + nh + 255) / 256;
+    int64_t blocks = (nw + nh + 8 * 256 - 1) / (8 * 256);
     if (blocks > 8 * kNumSMs) blocks = 8 * kNumSMs;
     *it = FinalizeItem{nw, nh, W, H, Wy, Hy, Wn, Hn, Hw, state, p};
     *ctas = blocks;
