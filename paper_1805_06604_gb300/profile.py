@@ -33,6 +33,9 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=0,
                     help="time COUNT uneven instances (m, n ~ U{64..2048}, r ~ U{4..32}): "
                          "batched graph vs per-instance launch loop")
+    ap.add_argument("--plan", default="",
+                    help="with --batch: GROUPED,BRANCHES,COLS -- set this schedule and run "
+                         "--iters iterations only (for a profiler's launch list)")
     args = ap.parse_args(argv)
     if args.batch:
         return batch_main(args)
@@ -71,6 +74,17 @@ def batch_main(args):
     t0 = time.perf_counter()
     b = nmf.Batch([(P.X, P.r, P.W0, P.H0) for P in probs])
     t_create = time.perf_counter() - t0
+    if args.plan:
+        g, br, cols = (int(v) for v in args.plan.split(","))
+        b.set_plan(g, br, cols)
+        b.step(max(args.iters, 1))
+        torch.cuda.synchronize()
+        pl = b.plan()
+        b.close()
+        print(json.dumps({"instances": args.batch, "grouped": pl.grouped, "branches": pl.branches,
+                          "h_cols": pl.h_cols_per_cta, "launches_per_iter": pl.launches_per_iter,
+                          "iters": max(args.iters, 1)}))
+        return
     branches, tuned = b.schedule()
     K = max(args.iters, 1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
