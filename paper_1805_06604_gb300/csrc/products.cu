@@ -30,6 +30,21 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, boo
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc),
                  "r"(src_bytes));
 }
+// The same for X, which each product reads exactly once: marked to leave L2
+// first, so that streaming it does not push out the factors and the split
+// partials that are read again.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void cp_async16_stream(void *smem_dst, const void *gsrc, bool pred,
+                                                  uint64_t pol) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const int src_bytes = pred ? 16 : 0;   // 0 -> zero fill
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;\n" ::"r"(d),
+                 "l"(gsrc), "r"(src_bytes), "l"(pol));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -75,6 +90,7 @@ xht_body(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     constexpr int kRowsPerPass = kThreads / (BK / 4);
     const int lr = tid / (BK / 4), c4 = tid % (BK / 4);
     const float *xg = X + (row0 + lr) * ldx + kbeg + c4 * 4;
+    const uint64_t pol = evict_first_policy();
     const float *hg = H + (int64_t)lr * ldh + kbeg + c4 * 4;
     auto load_stage = [&](int stage, int64_t kt) {
         const int64_t koff = kt * BK;
@@ -83,8 +99,8 @@ xht_body(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
 #pragma unroll
         for (int j = 0; j < BM / kRowsPerPass; ++j) {
             const bool ok = colok && row0 + lr + j * kRowsPerPass < m;
-            cp_async16(xs + j * kRowsPerPass * PADK,
-                       ok ? xg + (int64_t)j * kRowsPerPass * ldx + koff : X, ok);
+            cp_async16_stream(xs + j * kRowsPerPass * PADK,
+                              ok ? xg + (int64_t)j * kRowsPerPass * ldx + koff : X, ok, pol);
         }
         float *hs = Hs + stage * R * PADK + lr * PADK + c4 * 4;
 #pragma unroll
@@ -257,6 +273,7 @@ wtx_body(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
     const int64_t i_begin = (int64_t)split * rows_per_split;
     const int64_t i_end = min(m, i_begin + rows_per_split);
     const int64_t nk = i_end > i_begin ? (i_end - i_begin + BK - 1) / BK : 0;
+    const uint64_t pol = evict_first_policy();
 
     auto load_stage = [&](int stage, int64_t kt) {
         const int64_t i0 = i_begin + kt * BK;
@@ -265,7 +282,7 @@ wtx_body(const float *__restrict__ X, int64_t m, int64_t ldx, int r,
             const int ii = idx / (BN / 4), c4 = idx % (BN / 4);
             const int64_t grow = i0 + ii, gcol = col0 + c4 * 4;
             const bool ok = grow < i_end && gcol < ldx;
-            cp_async16(xs + ii * PADN + c4 * 4, ok ? X + grow * ldx + gcol : X, ok);
+            cp_async16_stream(xs + ii * PADN + c4 * 4, ok ? X + grow * ldx + gcol : X, ok, pol);
         }
         float *ws = Ws + stage * BK * PADR;
         for (int idx = tid; idx < BK * (R / 4); idx += NT) {

@@ -118,6 +118,23 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+// The same with an L2 eviction policy: the packed X is read exactly once per
+// product and is marked to leave L2 first, so that streaming it does not
+// push out the factors and the partials that are read again.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void bulk_load_stream(void *dst, const void *src, uint32_t bytes,
+                                                 uint64_t *bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
 // Nearest TF32 value of x (ties away from zero).  The MMA reads an FP32
 // operand's top 19 bits, i.e. it truncates: on nonnegative data that is a
 // bias of about -2^-11 relative in every product, which the Remark 1 error
@@ -361,6 +378,7 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
             int it = 0;
             bool ok = true, waited = false;
             int k0_def[kStages];
+            const uint64_t pol_x = evict_first_policy();
             auto issue_q = [&](int s, int k0) {
                 unsigned char *qs = smem + s * Cfg::kStageBytes + Cfg::kBoxes * Cfg::kPBytes;
 #pragma unroll
@@ -400,7 +418,8 @@ tc_gemm_kernel(const unsigned char *__restrict__ pk, const unsigned char *__rest
                         const unsigned char *src = ((KIND == 1 && b == 1) ? pk_lo : pk) +
                                                    (tile * ((int64_t)nk * Cfg::kAtoms) + atom) *
                                                        Cfg::kPBytes;
-                        bulk_load(st + b * Cfg::kPBytes, src, Cfg::kPBytes, &full_bar[s]);
+                        bulk_load_stream(st + b * Cfg::kPBytes, src, Cfg::kPBytes, &full_bar[s],
+                                         pol_x);
                     }
                     if (waited) issue_q(s, k0);
                     else k0_def[s] = k0;

@@ -490,3 +490,54 @@ def test_delta_rule_single_step(delta):
 
 def test_delta_rule_k_iterations():
     k_iteration_parity(300, 200, 8, 400, 3, 0.05, delta=0.1)
+
+
+@pytest.mark.parametrize("side", ["rows", "cols"])
+def test_permutation_equivariance(side):
+    """Metamorphic check through the C-ABI: permuting the rows of X and W0
+    (or the columns of X and H0) permutes the GPU's iterates.  Every update
+    acts per row of W / column of H; only the products' sums over the
+    permuted index run in another order, so the results agree to FP32
+    round-off, with the same accept/restart decisions."""
+    P = wl.low_rank(700, 530, 12, seed=21, noise=0.05)
+    perm = wl.rng(22).permutation(P.m if side == "rows" else P.n)
+    X, W0, H0 = f32(P.X), f32(P.W0), f32(P.H0)
+    if side == "rows":
+        Xp, W0p, H0p = X[perm], W0[perm], H0
+    else:
+        Xp, W0p, H0p = X[:, perm], W0, H0[:, perm]
+    K = 10
+    with nmf.Solver(X, P.r, W0, H0) as s, nmf.Solver(f32(Xp), P.r, f32(W0p), f32(H0p)) as sp:
+        s.step(K)
+        sp.step(K)
+        W, H = s.factors()
+        Wp, Hp = sp.factors()
+        te, _, ta = s.trace()
+        tep, _, tap = sp.trace()
+    np.testing.assert_array_equal(ta, tap)
+    np.testing.assert_allclose(te, tep, rtol=1e-5)
+    if side == "rows":
+        assert normwise(Wp, W[perm]) <= 1e-4 and normwise(Hp, H) <= 1e-4
+    else:
+        assert normwise(Wp, W) <= 1e-4 and normwise(Hp, H[:, perm]) <= 1e-4
+
+
+def test_power_of_two_scaling_is_exact():
+    """Metamorphic check through the C-ABI: X -> 4X, W0 -> 2W0, H0 -> 2H0
+    scales every product, Gram, update and error by a power of two, which
+    FP32 and FP64 arithmetic carry out exactly: the iterates are exactly
+    twice the unscaled ones, e(k) exactly four times, the decisions equal."""
+    P = wl.low_rank(640, 450, 16, seed=23, noise=0.05)
+    X, W0, H0 = f32(P.X), f32(P.W0), f32(P.H0)
+    K = 12
+    with nmf.Solver(X, P.r, W0, H0) as s, nmf.Solver(4 * X, P.r, 2 * W0, 2 * H0) as s4:
+        s.step(K)
+        s4.step(K)
+        W, H = s.factors()
+        W4, H4 = s4.factors()
+        te, _, ta = s.trace()
+        te4, _, ta4 = s4.trace()
+    np.testing.assert_array_equal(ta, ta4)
+    np.testing.assert_array_equal(4 * te, te4)
+    np.testing.assert_array_equal(2 * W, W4)
+    np.testing.assert_array_equal(2 * H, H4)
