@@ -163,6 +163,31 @@ def load_traffic(kernel: str):
     return ent.get("bytes_per_launch")
 
 
+def sgemm_tflops(n: int = 8192, reps: int = 5) -> float:
+    """A measured FP32 rate for the ALU roofline's context: cuBLAS SGEMM with
+    TF32 off (the FMA pipes, as the CUDA-core kernels use them)."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        g = torch.Generator(device="cuda").manual_seed(0)
+        a = torch.rand((n, n), device="cuda", generator=g)
+        b = torch.rand((n, n), device="cuda", generator=g)
+        c = a @ b
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            c = a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) / 1000.0 / reps
+        del a, b, c
+        return 2.0 * n ** 3 / s / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def timed_steps(solver, steps, stream):
     """Seconds for `steps` graph replays of `solver`, on the device clock."""
     import torch
@@ -544,6 +569,11 @@ def run_ours(args, world, rank, local):
                                         f"152 SMs x 128 lanes x 2 x {sm_max_mhz:.0f} MHz"),
                         "algorithmic_per_launch": {"flops": fl, "bytes": by},
                         "profiled_iters": prof_iters}
+    if unit == "TFLOP/s":
+        sg = sgemm_tflops()
+        line["roofline"]["measured_fp32"] = {
+            "sgemm_tflops": sg, "frac": achieved / sg if sg else None,
+            "what": "cuBLAS FP32 SGEMM 8192^3 (TF32 off), CUDA events, on this GPU"}
     # The X-streaming products against HBM (the metric's roofline).
     xbytes = {k: work[k][1] for k in ("wtx", "xht")}
     line["x_products_hbm"] = {k: {"gbs": xbytes[k] / (ms[k] / 1000.0) / 1e9,
