@@ -77,6 +77,7 @@ struct nmf_handle {
     int64_t *colptr = nullptr;                   // CSC of X (CSR of X^T)
     int32_t *rowidx = nullptr;
     float *cval = nullptr;
+    int32_t *rowseg = nullptr, *colseg = nullptr;  // row (CSR) / column (CSC) of each entry
     float *Ht = nullptr;                         // n x rs transpose of H_y' (CSR path)
     float *carry = nullptr;                      // chunk partials of the CSR products
     // factors and products
@@ -140,7 +141,8 @@ namespace {
 void free_handle(nmf_handle *h) {
     if (!h) return;
     if (h->exec) cudaGraphExecDestroy(h->exec);
-    void *ptrs[] = {h->X, h->rowptr, h->colidx, h->val, h->colptr, h->rowidx, h->cval, h->Ht,
+    void *ptrs[] = {h->X, h->rowptr, h->colidx, h->val, h->colptr, h->rowidx, h->cval, h->rowseg,
+                    h->colseg, h->Ht,
                     h->carry,
                     h->W, h->H, h->Wy, h->Hy, h->Wn, h->Hn, h->Hw, h->A, h->C, h->G, h->D,
                     h->C_lo, h->D_lo, h->G_lo, h->Wt, h->Wq, h->Hq, h->Pc, h->Pc_lo, h->Pa, h->Pa_lo, h->Wth,
@@ -184,7 +186,8 @@ inline int round16(int r) { return (r + 15) / 16 * 16; }
 // X products for the current layout and precision.
 cudaError_t enqueue_wtx(nmf_handle *h, const float *Wsrc, cudaStream_t st) {
     if (h->is_csr)
-        return launch_wtx_csc(h->colptr, h->rowidx, h->cval, h->n, h->nnz, h->r, h->rs, Wsrc, h->A,
+        return launch_wtx_csc(h->colptr, h->rowidx, h->colseg, h->cval, h->n, h->nnz, h->r, h->rs,
+                              Wsrc, h->A,
                               h->ld, h->carry, st);
     if (h->p.precision == NMF_PREC_FP32)
         return launch_wtx_f32(h->X, h->m, h->ld, h->ld, h->r, Wsrc, h->rs, h->A, h->ws,
@@ -213,7 +216,8 @@ cudaError_t enqueue_xht(nmf_handle *h, const float *Hsrc, cudaStream_t st) {
     if (h->is_csr) {
         cudaError_t e = launch_transpose_h(Hsrc, h->r, h->n, h->ld, h->Ht, h->rs, st);
         if (e != cudaSuccess) return e;
-        return launch_xht_csr(h->rowptr, h->colidx, h->val, h->m, h->nnz, h->r, h->rs, h->Ht, h->C,
+        return launch_xht_csr(h->rowptr, h->colidx, h->rowseg, h->val, h->m, h->nnz, h->r, h->rs,
+                              h->Ht, h->C,
                               h->carry, st);
     }
     if (h->p.precision == NMF_PREC_FP32)
@@ -740,6 +744,8 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
         NMF_TRYC(dalloc(&h->colptr, n + 1));
         NMF_TRYC(dalloc(&h->rowidx, nnz));
         NMF_TRYC(dalloc(&h->cval, nnz));
+        NMF_TRYC(dalloc(&h->rowseg, nnz));
+        NMF_TRYC(dalloc(&h->colseg, nnz));
         NMF_TRYC(dalloc(&h->Ht, n * rs));
         NMF_TRYC(dalloc(&h->carry, csr_carry_floats(nnz, (int)rs)));
         NMF_TRYC(cudaMemsetAsync(h->Ht, 0, sizeof(float) * n * rs, st));
@@ -756,6 +762,16 @@ nmf_status nmf_create(nmf_handle **out, const nmf_matrix *X, int32_t r, const fl
                                      cudaMemcpyHostToDevice, st));
             NMF_TRYC(cudaMemcpyAsync(h->cval, cv.data(), sizeof(float) * nnz,
                                      cudaMemcpyHostToDevice, st));
+            std::vector<int32_t> rsg(nnz), csg(nnz);
+            for (int64_t i = 0; i < m; ++i)
+                for (int64_t q = rp[i]; q < rp[i + 1]; ++q) rsg[q] = (int32_t)i;
+            for (int64_t j = 0; j < n; ++j)
+                for (int64_t q = cp[j]; q < cp[j + 1]; ++q) csg[q] = (int32_t)j;
+            NMF_TRYC(cudaMemcpyAsync(h->rowseg, rsg.data(), sizeof(int32_t) * nnz,
+                                     cudaMemcpyHostToDevice, st));
+            NMF_TRYC(cudaMemcpyAsync(h->colseg, csg.data(), sizeof(int32_t) * nnz,
+                                     cudaMemcpyHostToDevice, st));
+            NMF_TRYC(cudaStreamSynchronize(st));     // rsg, csg leave scope
         }
         NMF_TRYC(cudaStreamSynchronize(st));
         NMF_TRYC(launch_fro2(h->val, 1, nnz, nnz, h->fro2, h->ws, st));

@@ -326,12 +326,13 @@ cudaError_t launch_init_state(int64_t m, int r, int rs, const float *W, const fl
 // from the CSC copy; H (r x ldh) -> Ht.  `carry` holds csr_carry_floats()
 // floats of per-chunk partials.
 size_t csr_carry_floats(int64_t nnz, int rs);
-cudaError_t launch_xht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
-                           int64_t m, int64_t nnz, int r, int rs, const float *Ht, float *C,
-                           float *carry, cudaStream_t st);
-cudaError_t launch_wtx_csc(const int64_t *colptr, const int32_t *rowidx, const float *val,
-                           int64_t n, int64_t nnz, int r, int rs, const float *W, float *A,
-                           int64_t lda, float *carry, cudaStream_t st);
+// rowseg / colseg: the row (CSR) or column (CSC) of every stored entry.
+cudaError_t launch_xht_csr(const int64_t *rowptr, const int32_t *colidx, const int32_t *rowseg,
+                           const float *val, int64_t m, int64_t nnz, int r, int rs,
+                           const float *Ht, float *C, float *carry, cudaStream_t st);
+cudaError_t launch_wtx_csc(const int64_t *colptr, const int32_t *rowidx, const int32_t *colseg,
+                           const float *val, int64_t n, int64_t nnz, int r, int rs,
+                           const float *W, float *A, int64_t lda, float *carry, cudaStream_t st);
 cudaError_t launch_transpose_h(const float *H, int r, int64_t n, int64_t ldh, float *Ht, int rs,
                                cudaStream_t st);
 

@@ -22,18 +22,6 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int64_t kChunk = 256;
 
-__device__ __forceinline__ int64_t row_of(const int64_t *__restrict__ ptr, int64_t rows,
-                                          int64_t q) {
-    // Largest row with ptr[row] <= q (q < nnz).
-    int64_t lo = 0, hi = rows - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) / 2;
-        if (ptr[mid] <= q) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 template <int E>
 __device__ __forceinline__ void store_vec(float *dst, int64_t col_stride, const float (&acc)[E],
                                           int lane, int r) {
@@ -45,25 +33,29 @@ __device__ __forceinline__ void store_vec(float *dst, int64_t col_stride, const 
 }
 
 // out[row * ors + k * ocs] = sum_{q in row} val[q] * F[idx[q] * rs + k].
+// seg[q] is the row of stored entry q (expanded from ptr at creation), so a
+// row change is a register comparison, not a dependent load of ptr.
 // head[c] / tail[c] (rs floats each) receive the partials of rows cut by the
 // chunk boundaries.
 template <int E>
 __global__ void __launch_bounds__(kWarps * 32)
 spmm_chunks_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                   const float *__restrict__ val, int64_t rows, int64_t nnz, int r, int rs,
-                   const float *__restrict__ F, float *__restrict__ out, int64_t ors,
-                   int64_t ocs, float *__restrict__ head, float *__restrict__ tail) {
+                   const int32_t *__restrict__ seg, const float *__restrict__ val, int64_t nnz,
+                   int r, int rs, const float *__restrict__ F, float *__restrict__ out,
+                   int64_t ors, int64_t ocs, float *__restrict__ head, float *__restrict__ tail) {
     const int lane = threadIdx.x % 32;
     const int64_t c = (int64_t)blockIdx.x * kWarps + threadIdx.x / 32;
     const int64_t q0 = c * kChunk;
     if (q0 >= nnz) return;
-    const int64_t q1 = min(nnz, q0 + kChunk);
-    int64_t row = row_of(ptr, rows, q0);
-    int64_t row_end = ptr[row + 1];
+    const int n_here = (int)(nnz - q0 < kChunk ? nnz - q0 : kChunk);
+    int64_t row = seg[q0];
     bool started_before = ptr[row] < q0;
     float acc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[e] = 0.0f;
+    bool kok[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) kok[e] = lane + 32 * e < rs;
 
     auto flush = [&](bool continues) {
         float *dst;
@@ -81,14 +73,16 @@ spmm_chunks_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ 
         for (int e = 0; e < E; ++e) acc[e] = 0.0f;
     };
 
-    // The factor rows of kBatch nonzeros are gathered before any of them is
+    // The factor rows of kBatch entries are gathered before any of them is
     // used, so their L2 latencies overlap instead of adding up.
     constexpr int kBatch = E <= 2 ? 8 : 4;
-    for (int64_t base = q0; base < q1; base += 32) {
-        const int64_t q = base + lane;
-        const int32_t cidx = q < q1 ? idx[q] : 0;
-        const float v = q < q1 ? val[q] : 0.0f;
-        const int cnt = (q1 - base) < 32 ? (int)(q1 - base) : 32;
+    for (int base = 0; base < n_here; base += 32) {
+        const int ql = base + lane;
+        const bool in = ql < n_here;
+        const int32_t cidx = in ? idx[q0 + ql] : 0;
+        const float v = in ? val[q0 + ql] : 0.0f;
+        const int32_t rw = in ? seg[q0 + ql] : -1;
+        const int cnt = n_here - base < 32 ? n_here - base : 32;
         for (int u0 = 0; u0 < cnt; u0 += kBatch) {
             float fv[kBatch][E];
 #pragma unroll
@@ -96,48 +90,41 @@ spmm_chunks_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ 
                 const int32_t cu = __shfl_sync(0xffffffffu, cidx, (u0 + j) & 31);
                 const float *f = F + (int64_t)cu * rs;
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int k = lane + 32 * e;
-                    fv[j][e] = (u0 + j < cnt && k < rs) ? __ldg(f + k) : 0.0f;
-                }
+                for (int e = 0; e < E; ++e) fv[j][e] = kok[e] ? __ldg(f + lane + 32 * e) : 0.0f;
             }
 #pragma unroll
             for (int j = 0; j < kBatch; ++j) {
-                const int u = u0 + j;
-                const float vu = __shfl_sync(0xffffffffu, v, u & 31);
-                if (u < cnt) {
-                    const int64_t qu = base + u;
-                    while (qu >= row_end) {          // next non-empty row
+                const float vu = __shfl_sync(0xffffffffu, v, (u0 + j) & 31);
+                const int32_t ru = __shfl_sync(0xffffffffu, rw, (u0 + j) & 31);
+                if (u0 + j < cnt) {
+                    if (ru != row) {                         // the previous row ends here
                         flush(false);
                         started_before = false;
-                        ++row;
-                        row_end = ptr[row + 1];
+                        row = ru;
                     }
 #pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        const int k = lane + 32 * e;
-                        if (k < rs) acc[e] = fmaf(vu, fv[j][e], acc[e]);
-                    }
+                    for (int e = 0; e < E; ++e)
+                        if (kok[e]) acc[e] = fmaf(vu, fv[j][e], acc[e]);
                 }
             }
         }
     }
-    flush(row_end > q1);
+    flush(ptr[row + 1] > q0 + n_here);
 }
 
 // For every chunk whose last row starts inside it and continues past it:
 // tail[c] + head[c+1] + ... + head[c_end] in chunk order.
 template <int E>
 __global__ void __launch_bounds__(kWarps * 32)
-spmm_fixup_kernel(const int64_t *__restrict__ ptr, int64_t rows, int64_t nnz, int r, int rs,
-                  float *__restrict__ out, int64_t ors, int64_t ocs,
+spmm_fixup_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ seg, int64_t nnz,
+                  int r, int rs, float *__restrict__ out, int64_t ors, int64_t ocs,
                   const float *__restrict__ head, const float *__restrict__ tail) {
     const int lane = threadIdx.x % 32;
     const int64_t c = (int64_t)blockIdx.x * kWarps + threadIdx.x / 32;
     const int64_t q0 = c * kChunk;
     if (q0 >= nnz) return;
     const int64_t q1 = min(nnz, q0 + kChunk);
-    const int64_t row = row_of(ptr, rows, q1 - 1);
+    const int64_t row = seg[q1 - 1];
     if (ptr[row + 1] <= q1 || ptr[row] < q0) return;   // not a row that starts here and continues
     const int64_t c_end = (ptr[row + 1] - 1) / kChunk;
     float acc[E];
@@ -146,6 +133,9 @@ spmm_fixup_kernel(const int64_t *__restrict__ ptr, int64_t rows, int64_t nnz, in
         const int k = lane + 32 * e;
         acc[e] = k < rs ? tail[c * rs + k] : 0.0f;
     }
+    // In chunk order; the loads of eight chunks go out together (a row of
+    // a frequent term spans many chunks).
+#pragma unroll 8
     for (int64_t cc = c + 1; cc <= c_end; ++cc) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -157,29 +147,33 @@ spmm_fixup_kernel(const int64_t *__restrict__ ptr, int64_t rows, int64_t nnz, in
 }
 
 template <int E>
-cudaError_t spmm_launch(const int64_t *ptr, const int32_t *idx, const float *val, int64_t rows,
-                        int64_t nnz, int r, int rs, const float *F, float *out, int64_t ors,
-                        int64_t ocs, float *head, float *tail, cudaStream_t st) {
+cudaError_t spmm_launch(const int64_t *ptr, const int32_t *idx, const int32_t *seg,
+                        const float *val, int64_t rows, int64_t nnz, int r, int rs, const float *F,
+                        float *out, int64_t ors, int64_t ocs, float *head, float *tail,
+                        cudaStream_t st) {
+    (void)rows;
     const int64_t chunks = (nnz + kChunk - 1) / kChunk;
     const unsigned grid = (unsigned)((chunks + kWarps - 1) / kWarps);
     if (grid == 0) return cudaSuccess;
-    spmm_chunks_kernel<E><<<grid, kWarps * 32, 0, st>>>(ptr, idx, val, rows, nnz, r, rs, F, out,
+    spmm_chunks_kernel<E><<<grid, kWarps * 32, 0, st>>>(ptr, idx, seg, val, nnz, r, rs, F, out,
                                                         ors, ocs, head, tail);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    spmm_fixup_kernel<E><<<grid, kWarps * 32, 0, st>>>(ptr, rows, nnz, r, rs, out, ors, ocs, head,
+    spmm_fixup_kernel<E><<<grid, kWarps * 32, 0, st>>>(ptr, seg, nnz, r, rs, out, ors, ocs, head,
                                                        tail);
     return cudaGetLastError();
 }
 
-cudaError_t spmm(const int64_t *ptr, const int32_t *idx, const float *val, int64_t rows,
-                 int64_t nnz, int r, int rs, const float *F, float *out, int64_t ors, int64_t ocs,
-                 float *head, float *tail, cudaStream_t st) {
+cudaError_t spmm(const int64_t *ptr, const int32_t *idx, const int32_t *seg, const float *val,
+                 int64_t rows, int64_t nnz, int r, int rs, const float *F, float *out, int64_t ors,
+                 int64_t ocs, float *head, float *tail, cudaStream_t st) {
     switch ((rs + 31) / 32) {
-        case 1: return spmm_launch<1>(ptr, idx, val, rows, nnz, r, rs, F, out, ors, ocs, head, tail, st);
-        case 2: return spmm_launch<2>(ptr, idx, val, rows, nnz, r, rs, F, out, ors, ocs, head, tail, st);
-        case 3: return spmm_launch<3>(ptr, idx, val, rows, nnz, r, rs, F, out, ors, ocs, head, tail, st);
-        case 4: return spmm_launch<4>(ptr, idx, val, rows, nnz, r, rs, F, out, ors, ocs, head, tail, st);
+#define NMF_SPMM_CASE(EV)                                                                     \
+    case EV:                                                                                  \
+        return spmm_launch<EV>(ptr, idx, seg, val, rows, nnz, r, rs, F, out, ors, ocs, head,   \
+                               tail, st);
+        NMF_SPMM_CASE(1) NMF_SPMM_CASE(2) NMF_SPMM_CASE(3) NMF_SPMM_CASE(4)
+#undef NMF_SPMM_CASE
         default: return cudaErrorInvalidValue;
     }
 }
@@ -211,23 +205,25 @@ size_t csr_carry_floats(int64_t nnz, int rs) {
 }
 
 // C (m x rs) = X H^T; the whole of C is rewritten (rows without entries are 0).
-cudaError_t launch_xht_csr(const int64_t *rowptr, const int32_t *colidx, const float *val,
-                           int64_t m, int64_t nnz, int r, int rs, const float *Ht, float *C,
-                           float *carry, cudaStream_t st) {
+cudaError_t launch_xht_csr(const int64_t *rowptr, const int32_t *colidx, const int32_t *rowseg,
+                           const float *val, int64_t m, int64_t nnz, int r, int rs,
+                           const float *Ht, float *C, float *carry, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(C, 0, sizeof(float) * (size_t)m * rs, st);
     if (e != cudaSuccess) return e;
     const size_t half = csr_carry_floats(nnz, rs) / 2;
-    return spmm(rowptr, colidx, val, m, nnz, r, rs, Ht, C, rs, 1, carry, carry + half, st);
+    return spmm(rowptr, colidx, rowseg, val, m, nnz, r, rs, Ht, C, rs, 1, carry, carry + half,
+                st);
 }
 
 // A (r x lda) = W^T X from the CSC copy; columns without entries are 0.
-cudaError_t launch_wtx_csc(const int64_t *colptr, const int32_t *rowidx, const float *val,
-                           int64_t n, int64_t nnz, int r, int rs, const float *W, float *A,
-                           int64_t lda, float *carry, cudaStream_t st) {
+cudaError_t launch_wtx_csc(const int64_t *colptr, const int32_t *rowidx, const int32_t *colseg,
+                           const float *val, int64_t n, int64_t nnz, int r, int rs,
+                           const float *W, float *A, int64_t lda, float *carry, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(A, 0, sizeof(float) * (size_t)r * lda, st);
     if (e != cudaSuccess) return e;
     const size_t half = csr_carry_floats(nnz, rs) / 2;
-    return spmm(colptr, rowidx, val, n, nnz, r, rs, W, A, 1, lda, carry, carry + half, st);
+    return spmm(colptr, rowidx, colseg, val, n, nnz, r, rs, W, A, 1, lda, carry, carry + half,
+                st);
 }
 
 cudaError_t launch_transpose_h(const float *H, int r, int64_t n, int64_t ldh, float *Ht, int rs,

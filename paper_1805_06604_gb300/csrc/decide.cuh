@@ -9,6 +9,27 @@
 
 namespace nmfg {
 
+// Double-float accumulation (hi + lo in FP32) of sums of x * (a + a_lo), the
+// per-row error terms of Remark 1: FP32 error-free steps (rounded
+// intrinsics, so nothing is contracted) instead of FP64 arithmetic, whose
+// pipe on this GPU is a small fraction of the FP32 one.  Over a row of r
+// terms the result is exact to about r 2^-48 relative.
+struct DFAcc {
+    float h = 0.0f, l = 0.0f;
+};
+__device__ __forceinline__ void df_add_prod(DFAcc &acc, float x, float a, float a_lo) {
+    const float p = __fmul_rn(x, a);
+    const float pe = __fmaf_rn(x, a, -p);                      // x a = p + pe exactly
+    const float t = __fadd_rn(acc.h, p);
+    const float bb = __fsub_rn(t, acc.h);
+    const float e = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    acc.l = __fadd_rn(acc.l, __fadd_rn(e, __fmaf_rn(x, a_lo, pe)));
+    acc.h = t;
+}
+__device__ __forceinline__ double df_value(const DFAcc &acc) {
+    return (double)acc.h + (double)acc.l;
+}
+
 // Algorithm 3 and steps 16-20 of Algorithm 2, run by one thread.
 __device__ __forceinline__ void decide_and_update_beta(DevState *s, const DevParams &p, const DevTrace &t,
                                        double cross, double quad, double bnum, double bden) {

@@ -378,14 +378,15 @@ hals_body(int64_t items, int r, int64_t ld,
                 hi[s] = sum;
             }
         }
-        double cross = 0.0, quad = 0.0;
+        DFAcc cacc, qacc;
         if (valid) {
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                cross = fma((double)x[s], (double)a[s] + (double)clo[s], cross);
-                quad = fma((double)x[s], (double)hi[s] + (double)lo[s], quad);
+                df_add_prod(cacc, x[s], a[s], clo[s]);
+                df_add_prod(qacc, x[s], hi[s], lo[s]);
             }
         }
+        double cross = df_value(cacc), quad = df_value(qacc);
         // Line-search diagnostic (Sec. 3): with the direction
         // dW = W_n - W (W the accepted iterate), beta* = num / den where
         //   num = <X - W_n H_y, dW H_y> = -<W_n D - C, dW>,
