@@ -106,7 +106,8 @@ nnls_kernel(int64_t items, int r, int64_t ld,
     }
     const unsigned full = 0xffffffffu;
     const int max_iter = 100 * (r + 1);
-    double cross = 0.0, quad = 0.0, bnum = 0.0, bden = 0.0;
+    DFAcc cacc, qacc;                      // Remark 1 terms (double-float FP32)
+    double bnum = 0.0, bden = 0.0;
     int bad_status = 0;
 
     for (int64_t item = (int64_t)blockIdx.x * kAnlsWarps + warp; item < items;
@@ -313,8 +314,8 @@ nnls_kernel(int64_t items, int r, int64_t ld,
                     hi = sum;
                     if (ls) dd = fmaf(dh, ws.z[i], dd);
                 }
-                cross = fma((double)xv[s], (double)c + (double)clo, cross);
-                quad = fma((double)xv[s], (double)hi + (double)lo, quad);
+                df_add_prod(cacc, xv[s], c, clo);
+                df_add_prod(qacc, xv[s], hi, lo);
                 if (ls) {
                     // Line-search diagnostic of Sec. 3 (see hals_impl.cuh).
                     const float dk = ws.z[k];
@@ -330,8 +331,8 @@ nnls_kernel(int64_t items, int r, int64_t ld,
     if constexpr (ERR) {
         __shared__ double red[4][kAnlsWarps];
         __shared__ bool am_last;
-        cross = warp_sum_d(cross);
-        quad = warp_sum_d(quad);
+        double cross = warp_sum_d(df_value(cacc));
+        double quad = warp_sum_d(df_value(qacc));
         bnum = warp_sum_d(bnum);
         bden = warp_sum_d(bden);
         if (lane == 0) {
