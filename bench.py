@@ -188,6 +188,28 @@ def sgemm_tflops(n: int = 8192, reps: int = 5) -> float:
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
+def l2_copy_gbs(mb: int = 24, reps: int = 200) -> float:
+    """A measured L2 rate for the sparse products' gathers: device-to-device
+    copies of a 24 MB buffer (source and destination stay in the 129 MB L2),
+    read plus written bytes per second."""
+    import torch
+    n = mb * (1 << 20) // 4
+    a = torch.rand(n, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        b.copy_(a)
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1000.0
+    del a, b
+    return 2.0 * 4 * n * reps / s / 1e9
+
+
 def timed_steps(solver, steps, stream):
     """Seconds for `steps` graph replays of `solver`, on the device clock."""
     import torch
@@ -276,6 +298,8 @@ def other_workloads(nmf, torch, stream):
     pm = sv.profile_phases(10)
     sv.close()
     hbm_gbs = peaks()[0]
+    l2_gbs = l2_copy_gbs()
+    doc["l2_copy_gbs_measured"] = l2_gbs
     nnz = float(P.nnz)
     for k in ("wtx", "xht"):
         s_ = pm[k] / 1000.0
@@ -283,7 +307,8 @@ def other_workloads(nmf, torch, stream):
         gathered = 4.0 * P.r * nnz
         doc[k] = {"us": pm[k] * 1000.0, "stored_gbs": stored / s_ / 1e9,
                   "frac_of_hbm": stored / s_ / 1e9 / hbm_gbs,
-                  "gathered_gbs": gathered / s_ / 1e9}
+                  "gathered_gbs": gathered / s_ / 1e9,
+                  "gathered_frac_of_l2": gathered / s_ / 1e9 / l2_gbs if l2_gbs else None}
     out["document_like_csr"] = doc
     # E-ANLS (exact NNLS subproblems, nmf_params.exact_nnls) and the A-HALS
     # inner stopping rule (delta = 0.1) on the dense noisy workload.

@@ -93,8 +93,11 @@ def test_solver_single_step_precision_modes(prec):
 def test_precision_study_image_like_small():
     """The precision study on a reduced image-like matrix: FP32 CUDA cores,
     TF32 and split BF16 against the FP64 oracle after K iterations.  Prints
-    the errors; BF16X3 must stay within 1e-3 relative of the oracle's final
-    error and TF32 within 3e-2."""
+    the errors; both tensor-core modes must stay within 1e-3 relative of
+    the oracle's final error (measured: TF32 8.8e-5, BF16X3 1.2e-4 after 60
+    unconverged iterations; TF32 factors X rounded to 10 mantissa bits, about
+    2e-4 relative RMS from X, which bounds how close it can come).  The
+    full-size image-like run (tests/test_gpu_fullsize_k.py) holds both at 1e-4."""
     P = wl.image_like(seed=3, grid=(32, 28), n=600, r=16, blobs=16)
     p = oracle_params(P)
     Xo = oracle_X(P)
@@ -117,7 +120,7 @@ def test_precision_study_image_like_small():
         print(f"  {k:7s} {v[0]:.6e} {v[1]:.2e} {v[2]:.2e} {v[3]:.2e}")
     assert report["fp32"][1] <= 1e-4
     assert report["bf16x3"][1] <= 1e-3
-    assert report["tf32"][1] <= 3e-2
+    assert report["tf32"][1] <= 1e-3
 
 
 @pytest.mark.parametrize("prec", [nmf.NMF_PREC_TF32, nmf.NMF_PREC_BF16X3])
