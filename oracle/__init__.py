@@ -82,6 +82,8 @@ def _load():
         "orc_hals_sweeps_w": (None, [ct.c_int64, ct.c_int, _DP, _DP, _DP, ct.c_int]),
         "orc_hals_sweeps_h_delta": (ct.c_int, [ct.c_int64, ct.c_int, _DP, _DP, _DP, ct.c_int,
                                                ct.c_double]),
+        "orc_hals_sweeps_w_delta": (ct.c_int, [ct.c_int64, ct.c_int, _DP, _DP, _DP, ct.c_int,
+                                               ct.c_double]),
         "orc_err2_expanded": (ct.c_double, [ct.c_double, ct.c_int64, ct.c_int, _DP, _DP, _DP]),
         "orc_err2_direct": (ct.c_double, [vp, ct.c_int, _DP, _DP]),
         "orc_sweep_counts": (None, [ct.c_int64, ct.c_int64, ct.c_int64, ct.c_int, ct.c_double,
@@ -264,6 +266,14 @@ def hals_sweeps_h_delta(A, G, H, max_sweeps, delta):
     used = _load().orc_hals_sweeps_h_delta(H.shape[1], H.shape[0], _ptr(A), _ptr(G), _ptr(H),
                                            int(max_sweeps), float(delta))
     return H, used
+
+
+def hals_sweeps_w_delta(C, D, W, max_sweeps, delta):
+    """The W side of the inner stopping rule; returns (W, sweeps done)."""
+    C, D, W = _f64(C), _f64(D), _f64(W).copy()
+    used = _load().orc_hals_sweeps_w_delta(W.shape[0], W.shape[1], _ptr(C), _ptr(D), _ptr(W),
+                                           int(max_sweeps), float(delta))
+    return W, used
 
 
 def hals_sweeps_w(C, D, W, sweeps) -> np.ndarray:

@@ -721,6 +721,36 @@ def test_delta_rule_stops_where_the_definition_says(delta):
         assert used == 30
 
 
+@pytest.mark.parametrize("delta", [1e-12, 0.5, 0.1])
+def test_delta_rule_w_side_stops_where_the_definition_says(delta):
+    """orc_hals_sweeps_w_delta against the same rule evaluated with numpy
+    over single sweeps of the rows of W: stop after the first sweep l >= 2
+    with ||W^(l) - W^(l-1)||_F <= delta ||W^(1) - W^(0)||_F (cap 25), and
+    the result equals that many plain sweeps bit for bit."""
+    P = wl.low_rank(50, 45, 5, seed=34, noise=0.05, dtype=np.float64)
+    H = _rand((5, 45), 35)
+    C, D = O.xht(P.X, H), O.gram_h(H)
+    W0 = _rand((50, 5), 36)
+    Wd, used = O.hals_sweeps_w_delta(C, D, W0, 25, delta)
+    W = W0.copy()
+    first, want = None, 25
+    for l in range(1, 26):
+        Wn = O.hals_sweeps_w(C, D, W, 1)
+        d = np.linalg.norm(Wn - W)
+        W = Wn
+        if l == 1:
+            first = d
+        elif d <= delta * first:
+            want = l
+            break
+    assert used == want
+    np.testing.assert_array_equal(Wd, O.hals_sweeps_w(C, D, W0, used))
+    if delta >= 0.5:
+        assert used < 25
+    if delta == 1e-12:
+        assert used == 25
+
+
 def test_delta_rule_in_the_step_reports_its_sweeps():
     P = wl.low_rank(50, 40, 5, seed=33, noise=0.05, dtype=np.float64)
     p = O.Params(hp=3, lw=20, lh=25, delta=0.1)
