@@ -154,22 +154,34 @@ nnls_kernel(int64_t items, int r, int64_t ld,
                 ws.L[e] = Gs[ws.F[a] * rq + ws.F[c]];
             }
             __syncwarp();
+            // Left-looking: column c from the finished columns before it,
+            // the diagonal by a warp sum over row c, the rows below one per
+            // lane (a dot product each), so a column is one parallel step.
             bool pd = true;
-            for (int c = 0; c < nf && pd; ++c) {
-                const float d = ws.L[tri(c) + c];
+            for (int c = 0; c < nf; ++c) {
+                float part = 0.0f;
+                for (int k = lane; k < c; k += 32) {
+                    const float v = ws.L[tri(c) + k];
+                    part = fmaf(v, v, part);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(full, part, o);
+                part = __shfl_sync(full, part, 0);          // one value for the whole warp
+                const float d = ws.L[tri(c) + c] - part;
                 if (!(d > 0.0f)) {
                     pd = false;
                     break;
                 }
                 const float lc = sqrtf(d), ilc = 1.0f / lc;
-                __syncwarp();
-                for (int i = c + 1 + lane; i < nf; i += 32) ws.L[tri(i) + c] *= ilc;
-                if (lane == 0) ws.L[tri(c) + c] = lc;
-                __syncwarp();
-                for (int j = c + 1; j < nf; ++j) {
-                    const float ljc = ws.L[tri(j) + c];
-                    for (int i = j + lane; i < nf; i += 32) ws.L[tri(i) + j] -= ws.L[tri(i) + c] * ljc;
+                const float *lrow = ws.L + tri(c);
+                for (int i = c + 1 + lane; i < nf; i += 32) {
+                    const float *irow = ws.L + tri(i);
+                    float sdot = irow[c];
+                    for (int k = 0; k < c; ++k) sdot = fmaf(-irow[k], lrow[k], sdot);
+                    ws.L[tri(i) + c] = sdot * ilc;
                 }
+                __syncwarp();
+                if (lane == 0) ws.L[tri(c) + c] = lc;
                 __syncwarp();
             }
             if (!pd) break;
